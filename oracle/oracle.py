@@ -1,0 +1,254 @@
+"""CPU oracle for the conditional beta draw (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The library never does.  It wraps the
+plain C FP64 routines in ``pcg_oracle.c`` and composes them, step by step,
+into the draw of Prop. 2.1 (right-hand side by Eq. 2.3, then Phi beta = b by
+Eq. 2.4):
+
+* ``draw_beta_cg``   -- prior-preconditioned CG (Sec. 2.4, Algorithm S1,
+                        stop rule Eq. S2);
+* ``draw_beta_chol`` -- the direct sampler: dense Phi, Cholesky, two
+                        triangular solves (Sec. 1);
+* ``adjoint``        -- gradient of L = c^T beta, by implicit differentiation
+                        of beta = Phi^-1 b (not in the paper; derivation in
+                        the docstring).
+
+Every function takes the same numpy inputs as the CUDA path (see
+``paper_1810_12437_gb300.inputs``).  Parity: each routine is pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sysconfig
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pcg_oracle.c")
+_LIB = os.path.join(_HERE, "_pcg_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STOP_RMS = 0
+STOP_RELATIVE = 1
+OK, MAXITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile pcg_oracle.c into _pcg_oracle.so with gcc (plain -O2, no
+    vector extensions, so that x86 and Arm builds round identically)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(lib):
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    D = ctypes.c_double
+    I = ctypes.c_int
+    lib.oracle_x_mul.argtypes = [I64, P, P, P, P]
+    lib.oracle_xt_mul.argtypes = [I64, P, P, P, P]
+    lib.oracle_phi_mul.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P]
+    lib.oracle_build_b.argtypes = [I64, I64, P, P, P, P, P, D, P, P, P, P]
+    lib.oracle_pcg.argtypes = [I64, I64, P, P, P, P, P, P, D, P, D, I, I, I, P, P, P, P]
+    lib.oracle_pcg.restype = I
+    lib.oracle_dense_phi.argtypes = [I64, I64, P, P, P, P, D, P]
+    lib.oracle_cholesky.argtypes = [I64, P]
+    lib.oracle_cholesky.restype = I
+    lib.oracle_chol_solve.argtypes = [I64, P, P, P]
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def use_library(path):
+    """Bind the oracle to another build of pcg_oracle.c (the mutation tests
+    compile deliberately broken copies and check that the pins reject them).
+    Returns the previously bound library so it can be restored."""
+    global _lib
+    _load()
+    with _lock:
+        prev = _lib
+        _lib = _bind(ctypes.CDLL(path)) if isinstance(path, str) else path
+    return prev
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def x_mul(X, v):
+    """X v for binary CSR X."""
+    lib = _load()
+    v = _f64(v)
+    out = np.empty(X.n)
+    lib.oracle_x_mul(X.n, _p(X.row_ptr), _p(X.col_idx), _p(v), _p(out))
+    return out
+
+
+def xt_mul(X, w):
+    """X^T w for binary CSC X."""
+    lib = _load()
+    w = _f64(w)
+    out = np.empty(X.p)
+    lib.oracle_xt_mul(X.p, _p(X.col_ptr), _p(X.row_idx), _p(w), _p(out))
+    return out
+
+
+def phi_mul(X, omega, lam, tau, v):
+    """Phi v = X^T Omega X v + tau^-2 lambda^-2 v, matrix-free (Sec. 1)."""
+    lib = _load()
+    omega, lam, v = _f64(omega), _f64(lam), _f64(v)
+    out = np.empty(X.p)
+    work = np.empty(max(X.n, 1))
+    lib.oracle_phi_mul(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr), _p(X.row_idx),
+                       _p(omega), _p(lam), float(tau), _p(v), _p(out), _p(work))
+    return out
+
+
+def build_b(X, omega, z, lam, tau, eta, delta):
+    """Right-hand side b of Prop. 2.1, Eq. 2.3."""
+    lib = _load()
+    omega, z, lam, eta, delta = map(_f64, (omega, z, lam, eta, delta))
+    b = np.empty(X.p)
+    work = np.empty(X.n + X.p + 1)
+    lib.oracle_build_b(X.n, X.p, _p(X.col_ptr), _p(X.row_idx), _p(omega), _p(z), _p(lam),
+                       float(tau), _p(eta), _p(delta), _p(b), _p(work))
+    return b
+
+
+def pcg(X, omega, lam, tau, b, *, tol=1e-6, stop_rule=STOP_RMS, max_iter=10_000,
+        fixed_iters=0, want_hist=False):
+    """Prior-preconditioned CG from beta_0 = 0 (Algorithm S1 in PCG form).
+
+    Returns (beta, iters, resid, status[, rho_hist]).  ``fixed_iters > 0``
+    runs exactly that many iterations with no stop test.
+    """
+    lib = _load()
+    omega, lam, b = _f64(omega), _f64(lam), _f64(b)
+    beta = np.empty(X.p)
+    iters = ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    hist = np.full(max(max_iter, fixed_iters) + 1, np.nan) if want_hist else None
+    st = lib.oracle_pcg(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr), _p(X.row_idx),
+                        _p(omega), _p(lam), float(tau), _p(b), float(tol), int(stop_rule),
+                        int(max_iter), int(fixed_iters), _p(beta), ctypes.byref(iters),
+                        ctypes.byref(resid), _p(hist) if want_hist else None)
+    out = (beta, iters.value, resid.value, st)
+    if want_hist:
+        out = out + (hist[: iters.value + 1],)
+    return out
+
+
+def dense_phi(X, omega, lam, tau):
+    """Dense Phi = X^T Omega X + tau^-2 Lambda^-2 (Eq. 1.2)."""
+    lib = _load()
+    omega, lam = _f64(omega), _f64(lam)
+    phi = np.empty((X.p, X.p))
+    lib.oracle_dense_phi(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(omega), _p(lam),
+                         float(tau), _p(phi))
+    return phi
+
+
+def cholesky(a):
+    """Lower Cholesky factor of an SPD matrix (plain column algorithm)."""
+    lib = _load()
+    l = np.array(a, dtype=np.float64, order="C", copy=True)
+    rc = lib.oracle_cholesky(l.shape[0], _p(l))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"matrix not positive definite at column {-1 - rc}")
+    return l
+
+
+def chol_solve(l, b):
+    """x = (L L^T)^-1 b."""
+    lib = _load()
+    b = _f64(b)
+    x = np.empty_like(b)
+    lib.oracle_chol_solve(l.shape[0], _p(l), _p(b), _p(x))
+    return x
+
+
+def draw_beta_chol(X, omega, z, lam, tau, eta, delta):
+    """Direct sampler: b by Eq. 2.3, then beta = Phi^-1 b by dense Cholesky."""
+    b = build_b(X, omega, z, lam, tau, eta, delta)
+    l = cholesky(dense_phi(X, omega, lam, tau))
+    return chol_solve(l, b)
+
+
+def draw_beta_cg(X, omega, z, lam, tau, eta, delta, *, tol=1e-6, stop_rule=STOP_RMS,
+                 max_iter=10_000, fixed_iters=0):
+    """CG sampler of Prop. 2.1: b by Eq. 2.3, then PCG on Eq. 2.4.
+
+    Returns (beta, iters, resid, status)."""
+    b = build_b(X, omega, z, lam, tau, eta, delta)
+    return pcg(X, omega, lam, tau, b, tol=tol, stop_rule=stop_rule, max_iter=max_iter,
+               fixed_iters=fixed_iters)
+
+
+def adjoint_from_g(X, omega, z, lam, tau, eta, delta, beta, g, mode="draw"):
+    """Gradient of L = c^T beta given beta = Phi^-1 b and g = Phi^-1 c.
+
+    beta = Phi^-1 b with Phi = X^T Omega X + diag(d), d_j = tau^-2 lambda_j^-2,
+    so dL = g^T db - g^T dPhi beta (Phi symmetric).  Hence, through Phi:
+        dL/domega_i     = -(X g)_i (X beta)_i
+        dL/dlog lambda_j = 2 d_j g_j beta_j        (dd_j/dlog lambda_j = -2 d_j)
+        dL/dlog tau      = sum_j 2 d_j g_j beta_j
+        dL/db            = g.
+    In "draw" mode b is built inside by Eq. 2.3 from (z, eta, delta) held
+    fixed, which adds, through b:
+        dL/domega_i     += (X g)_i (z_i + eta_i / (2 sqrt(omega_i)))
+        dL/dlog lambda_j += -g_j delta_j / (tau lambda_j)
+        dL/dlog tau      += -sum_j g_j delta_j / (tau lambda_j).
+    Returns dict(b=, omega=, log_lambda=, log_tau=).
+    """
+    omega, z, lam, eta, delta, beta, g = map(_f64, (omega, z, lam, eta, delta, beta, g))
+    d = 1.0 / (tau * tau * lam * lam)
+    xg = x_mul(X, g)
+    xb = x_mul(X, beta)
+    g_omega = -xg * xb
+    g_loglam = 2.0 * d * g * beta
+    if mode == "draw":
+        g_omega = g_omega + xg * (z + eta / (2.0 * np.sqrt(omega)))
+        g_loglam = g_loglam - g * delta / (tau * lam)
+    elif mode != "solve":
+        raise ValueError(mode)
+    return dict(b=g.copy(), omega=g_omega, log_lambda=g_loglam, log_tau=float(g_loglam.sum()))
+
+
+def adjoint_chol(X, omega, z, lam, tau, eta, delta, c, mode="draw"):
+    """Dense-Cholesky reference gradient: beta and g = Phi^-1 c by Cholesky."""
+    b = build_b(X, omega, z, lam, tau, eta, delta)
+    l = cholesky(dense_phi(X, omega, lam, tau))
+    beta = chol_solve(l, b)
+    g = chol_solve(l, c)
+    return beta, adjoint_from_g(X, omega, z, lam, tau, eta, delta, beta, g, mode)
+
+
+def adjoint_cg(X, omega, z, lam, tau, eta, delta, c, *, tol=1e-12, stop_rule=STOP_RMS,
+               max_iter=10_000, mode="draw"):
+    """Gradient with beta and g = Phi^-1 c both by the oracle's PCG."""
+    b = build_b(X, omega, z, lam, tau, eta, delta)
+    beta = pcg(X, omega, lam, tau, b, tol=tol, stop_rule=stop_rule, max_iter=max_iter)[0]
+    g = pcg(X, omega, lam, tau, c, tol=tol, stop_rule=stop_rule, max_iter=max_iter)[0]
+    return beta, adjoint_from_g(X, omega, z, lam, tau, eta, delta, beta, g, mode)

@@ -1,0 +1,93 @@
+"""Plant plausible mistakes in a copy of the oracle and check the pins catch them.
+
+Each mutant is a one-line textual change to ``oracle/pcg_oracle.c`` (a dropped
+term, a flipped sign, a wrong index or operand), compiled on the CPU into a
+temporary library.  The committed oracle is never modified.  A mutant passes
+this test only if at least one pin of ``test_oracle_pins`` rejects it.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "oracle", "pcg_oracle.c")
+
+MUTANTS = {
+    "drop_eta_term": ("        b[j] = b[j] + t[j];", "        b[j] = b[j];"),
+    "eta_without_sqrt": ("w[i] = sqrt(omega[i]) * eta[i];", "w[i] = omega[i] * eta[i];"),
+    "delta_term_squared_scale": ("b[j] = b[j] + delta[j] / (tau * lam[j]);",
+                                 "b[j] = b[j] + delta[j] / (tau * tau * lam[j] * lam[j]);"),
+    "residual_sign": ("r[j] = r[j] - alpha * v[j];", "r[j] = r[j] + alpha * v[j];"),
+    "wrong_preconditioner": ("z[j] = prior_var(tau, lam[j]) * r[j];\n            }",
+                             "z[j] = prior_prec(tau, lam[j]) * r[j];\n            }"),
+    "gamma_inverted": ("double gamma = rho_new / rho;", "double gamma = rho / rho_new;"),
+    "omega_index": ("work[i] = omega[i] * work[i];", "work[i] = omega[i / 2] * work[i];"),
+    "prior_diag_dropped": ("out[j] = out[j] + prior_prec(tau, lam[j]) * v[j];",
+                           "out[j] = out[j];"),
+    "xt_uses_wrong_index": ("acc += w[row_idx[k]];", "acc += w[row_idx[k] / 2];"),
+    "dense_phi_omega_index": ("+= omega[i];", "+= omega[col_idx[a] % n];"),
+    "chol_transposed_operand": ("e -= a[i * p + k] * a[j * p + k];", "e -= a[i * p + k] * a[k * p + j];"),
+    "rms_divisor": ("return sqrt(rho / (double)p) <= tol;", "return sqrt(rho) <= tol;"),
+    "beta_step_uses_v": ("beta[j] = beta[j] + alpha * s[j];", "beta[j] = beta[j] + alpha * v[j];"),
+}
+
+# the pins that run against each mutant (the slow statistical ones are left out:
+# every mutant below is caught by a deterministic pin)
+PIN_TESTS = [
+    pins.test_b_design_without_nonzeros_is_prior_term,
+    pins.test_b_single_row_by_hand,
+    pins.test_phi_mul_equals_dense_phi_times_v,
+    pins.test_xt_mul_is_transpose_of_x_mul,
+    pins.test_dense_phi_matches_numpy,
+    pins.test_cholesky_and_solve_match_lapack,
+    lambda: pins.test_direct_draw_equals_least_squares("small"),
+    pins.test_tiny_exact_rational_draw,
+    pins.test_cg_matches_cholesky_config1,
+    pins.test_cg_exact_after_p_iterations,
+    lambda: pins.test_thm22_low_rank_converges_in_k_plus_1(3),
+    pins.test_design_without_nonzeros_one_iteration,
+    pins.test_rho_is_true_preconditioned_residual,
+    pins.test_stop_rule_rms_is_first_crossing,
+    pins.test_thm21_error_bound_and_monotone_phi_norm_error,
+]
+
+
+def _caught(lib_path):
+    prev = O.use_library(lib_path)
+    try:
+        for t in PIN_TESTS:
+            try:
+                with np.errstate(all="ignore"):
+                    t()
+            except Exception:
+                return True
+        return False
+    finally:
+        O.use_library(prev)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    """Control: the same harness accepts an unmodified copy."""
+    src = open(SRC).read()
+    c = tmp_path / "ok.c"
+    c.write_text(src)
+    so = str(tmp_path / "ok.so")
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, str(c), "-lm"])
+    assert not _caught(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    c = tmp_path / f"{name}.c"
+    c.write_text(src.replace(old, new))
+    so = str(tmp_path / f"{name}.so")
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, str(c), "-lm"])
+    assert _caught(so), f"no pin rejects mutant {name}"
