@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the conditional beta draw on GB300.
+
+Workload (one step): 16 conditional draws of beta ~ N(Phi^-1 X^T Omega z,
+Phi^-1) sharing one synthetic binary design X with n = 500,000 rows and
+p = 50,000 columns (column rates log10 r ~ U(-4.5, -1.5), about 1.15e8
+nonzeros), each chain with its own omega, lambda, tau, eta and delta;
+right-hand sides by Eq. 2.3 and prior-preconditioned CG to the paper's RMS
+rule 1e-6 (Eq. S2), float32 products with float64 scalars and float64
+reliable updates, one batched launch (CUDA graph) per step.
+
+Printed (rank 0, one JSON line): beta-draws/s of the whole job, the
+end-to-end rate through the public API with host buffers, the roofline of the
+dominant kernel against the measured HBM peak, the oracle on the host cores,
+the plain single-RHS rate on the same GPU, clocks and kernel launch counts.
+
+`--impl reference` times the CPU oracle instead (the reference arm): each
+step is a bounded sample of the same workload (right-hand side plus a few CG
+iterations of one chain), scaled to draws/s with the oracle's own iteration
+counts for these chains (tests/golden/config3_oracle.json, written by a
+script that runs only the oracle).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "beta-draws/sec and SpMV HBM GB/s vs peak at n=5e5,p=5e4; batched/adjoint vs plain PCG"
+UNIT = "beta-draws/s"
+NRHS = 16
+TOL = 1e-6
+WORKLOAD = ("16 chains sharing binary X, n=500000, p=50000, log10 r_j~U(-4.5,-1.5), "
+            "per-chain omega~U(.05,.25), half-Cauchy lambda (2% x100), log10 tau~U(-3.5,-2.5), "
+            "paper RMS stop 1e-6")
+GOLDEN3 = os.path.join(ROOT, "tests", "golden", "config3_oracle.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single-RHS comparator, e2e and CPU baseline legs")
+    ap.add_argument("--small", action="store_true", help="debug: a 20x smaller design")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank, small):
+    from paper_1810_12437_gb300 import inputs
+    if small:
+        return inputs.config3(nrhs=NRHS, n=25_000, p=2_500, seed_offset=rank)
+    return inputs.config3(nrhs=NRHS, seed_offset=rank)
+
+
+def bytes_per_launch(kernel, n, p, nnz, RP):
+    """Algorithmic bytes of one launch of the batched kernels: every index read
+    once, every gathered vector read once (it is L2-resident), every output
+    written once."""
+    if kernel == "b_csr_f32":
+        return 4 * nnz + 8 * (n + 1) + 4 * n * RP + 4 * n * RP + 4 * p * RP
+    if kernel == "b_csc_f32":
+        return 4 * nnz + 8 * (p + 1) + 4 * n * RP + 3 * 8 * p * RP
+    if kernel == "b_ru_csr_f64":
+        return 4 * nnz + 8 * (n + 1) + 8 * n * RP + 8 * n * RP + 8 * p * RP
+    if kernel == "b_ru_true_resid":
+        return 4 * nnz + 8 * (p + 1) + 8 * n * RP + 5 * 8 * p * RP
+    if kernel in ("b_update",):
+        return 6 * 8 * p * RP
+    if kernel in ("b_sdir",):
+        return 3 * 8 * p * RP + 4 * p * RP
+    return None
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("batched.cu", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1810_12437_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """ncu DRAM bytes per launch from profiles/traffic.json, if they were taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_sha") == kernel_source_sha():
+            return e.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1810_12437_gb300 as pb
+
+    world, rank, local = dist_env()
+    if args.gpus != world and world > 1:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    P = make_workload(rank, args.small)
+    X = pb.DeviceDesign.from_host(P.X, dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    ins = dict(omega=T(P.omega), z=T(P.z), lam=T(P.lam), tau=T(P.tau), eta=T(P.eta), delta=T(P.delta))
+    out = torch.empty((NRHS, P.X.p), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream)
+
+    def step():
+        return pb.pcg_draw_beta_batched(ctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
+
+    res = None
+    for _ in range(args.warmup):
+        res = step()
+    # every step reads the 0.92 GB index streams of X, far larger than the
+    # 129 MB L2, so no separate flush is needed between steps
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    iters = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+        launches += pb.pcg_last_kernel_launches(ctx)
+        iters.append(list(res.iters))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * NRHS / (ms / 1e3)
+    statuses = list(res.status)
+
+    extras = {}
+    if not args.no_extras:
+        # plain single-RHS PCG on the same GPU and accuracy: the 16 chains one by one
+        sctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream)
+        s_iters = []
+        ch = lambda a, r: a[r].contiguous()
+        for r in range(NRHS):   # warm-up and graph capture on chain 0 first
+            if r == 0:
+                pb.pcg_draw_beta(sctx, X, ch(ins["omega"], 0), ch(ins["z"], 0), ch(ins["lam"], 0),
+                                 float(P.tau[0]), ch(ins["eta"], 0), ch(ins["delta"], 0), tol=TOL,
+                                 max_iter=20_000)
+        torch.cuda.synchronize(dev)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for r in range(NRHS):
+            rr = pb.pcg_draw_beta(sctx, X, ch(ins["omega"], r), ch(ins["z"], r), ch(ins["lam"], r),
+                                  float(P.tau[r]), ch(ins["eta"], r), ch(ins["delta"], r), tol=TOL,
+                                  max_iter=20_000)
+            s_iters.append(rr.iters)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        single_ms = s0.elapsed_time(s1)
+        extras["single_rhs"] = {"value": NRHS / (single_ms / 1e3), "unit": UNIT,
+                                "iters": s_iters, "note": "same 16 chains as 16 sequential "
+                                "single-RHS draws (plain PCG), same precision and stop rule"}
+        # end to end through the public API with host buffers (pinned)
+        host = {k: v.cpu().pin_memory() for k, v in ins.items()}
+        hout = torch.empty((NRHS, P.X.p), dtype=torch.float64).pin_memory()
+        dins = {k: torch.empty_like(v) for k, v in ins.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = hout.numel() * hout.element_size()
+
+        def e2e_step():
+            for k in host:
+                dins[k].copy_(host[k], non_blocking=True)
+            r_ = pb.pcg_draw_beta_batched(ctx, X, **dins, tol=TOL, max_iter=20_000, out=out)
+            hout.copy_(out, non_blocking=True)
+            return r_
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        ne = max(1, min(args.steps, 3))
+        for _ in range(ne):
+            e2e_step()
+        ee1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = ee0.elapsed_time(ee1) / ne
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        extras["e2e"] = {"value": world * NRHS / (e2e_ms / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                         "note": "X resident (fixed design); per-step chain inputs host->device"}
+
+    # roofline of the dominant kernel: per-kernel CUDA events on the launching stream
+    pctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream, profile=True)
+    pb.pcg_draw_beta_batched(pctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
+    table = pb.profile_table(pctx)
+    RP = 16
+    top = max(table.items(), key=lambda kv: kv[1][0])
+    kname, (kms, kn) = top
+    avg_s = kms / kn / 1e3
+    bpl = bytes_per_launch(kname, P.X.n, P.X.p, P.X.nnz, RP)
+    peak, peak_kind = peaks()
+    achieved = bpl / avg_s / 1e9 if bpl else None
+    total_ms = sum(v[0] for v in table.values())
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic_for(kname),
+            "peak_source": f"hbm_gbs of {peak_kind}", "avg_launch_us": avg_s * 1e6,
+            "algorithmic_bytes_per_launch": bpl,
+            "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in sorted(table.items())},
+            "per_kernel_GBps": {k: (bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP) / (v[0] / v[1] / 1e3) / 1e9
+                                    if bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP) else None)
+                                for k, v in sorted(table.items())}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        cpu = cpu_baseline(P, iters[-1])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": P.X.n, "p": P.X.p, "nnz": P.X.nnz, "nrhs": NRHS,
+                   "tol": TOL, "precision": "fp32 products, fp64 scalars, fp64 reliable update every 50",
+                   "parallelism": f"replicas x{world} (independent chains per GPU)",
+                   "l2": "inputs larger than L2 (0.92 GB of index streams per iteration)",
+                   "iters_per_chain": iters[-1], "status": statuses},
+        "e2e": extras.get("e2e"), "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "single_rhs": extras.get("single_rhs"), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, gpu_iters):
+    """The oracle, as it stands, on the host: chain 0's right-hand side plus 24
+    CG iterations, scaled to one full draw with chain 0's iteration count."""
+    from oracle import oracle as O
+    k_full, src = oracle_iters(P, 0, gpu_iters)
+    om, lam, tau = P.omega[0], P.lam[0], float(P.tau[0])
+    t0 = time.perf_counter()
+    b = O.build_b(P.X, om, P.z[0], lam, tau, P.eta[0], P.delta[0])
+    t1 = time.perf_counter()
+    S = 24
+    O.pcg(P.X, om, lam, tau, b, fixed_iters=S)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / S
+    draw_s = (t1 - t0) + per_iter * k_full
+    return {"value": 1.0 / draw_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"chain 0: RHS (Eq. 2.3) + {S} CG iterations ({t2 - t0:.1f} s), scaled to "
+                      f"{k_full} iterations ({src})",
+            "seconds_per_iteration": per_iter}
+
+
+def oracle_iters(P, r, gpu_iters=None):
+    try:
+        with open(GOLDEN3) as f:
+            g = json.load(f)
+        if g["nnz"] == P.X.nnz and g["n"] == P.X.n:
+            return int(g["chains"][r]["iters"]), "oracle iteration count, tests/golden/config3_oracle.json"
+    except Exception:
+        pass
+    if gpu_iters is not None:
+        return int(gpu_iters[r]), "GPU iteration count of the same chain"
+    return 1000, "assumed"
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    P = make_workload(0, args.small)
+    S = 4
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = k % NRHS
+        om, lam, tau = P.omega[r], P.lam[r], float(P.tau[r])
+        t0 = time.perf_counter()
+        b = O.build_b(P.X, om, P.z[r], lam, tau, P.eta[r], P.delta[r])
+        t1 = time.perf_counter()
+        O.pcg(P.X, om, lam, tau, b, fixed_iters=S)
+        t2 = time.perf_counter()
+        kf, src = oracle_iters(P, r)
+        if k >= args.warmup:
+            times.append((t1 - t0) + (t2 - t1) / S * kf)
+    per_draw = statistics.mean(times)
+    value = 1.0 / per_draw
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_draw * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": P.X.n, "p": P.X.p,
+                                             "nnz": P.X.nnz, "nrhs": NRHS, "tol": TOL},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": f"per step one chain: RHS + {S} CG iterations, scaled by "
+                                       f"that chain's iteration count ({src})"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

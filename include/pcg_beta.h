@@ -1,0 +1,230 @@
+/*
+ * pcg_beta.h -- C ABI of the GB300 library for the conditional draw of the
+ * regression coefficients in the CG-accelerated Gibbs sampler of Nishimura &
+ * Suchard, "Prior-preconditioned conjugate gradient method for accelerated
+ * Gibbs sampling in 'large n & large p' Bayesian sparse regression".
+ *
+ * The draw (Eq. 1.2 and Prop. 2.1):
+ *     beta ~ N(Phi^-1 X^T Omega z, Phi^-1),  Phi = X^T Omega X + tau^-2 Lambda^-2,
+ * computed as
+ *     b    = X^T Omega z + X^T Omega^1/2 eta + tau^-1 Lambda^-1 delta   (Eq. 2.3)
+ *     solve Phi beta = b                                              (Eq. 2.4)
+ * by conjugate gradient preconditioned with the prior precision
+ * M = tau^-2 Lambda^-2 (Sec. 2.4), from beta_0 = 0 (Sec. 2.7), with the
+ * recursion of Algorithm S1 (Sec. S2) in its preconditioned form and the
+ * stop rule of Eq. S2 (Sec. S4.2).  Phi is never formed: each iteration
+ * applies u = Omega (X s) and v = X^T u + tau^-2 Lambda^-2 s (Sec. 1).
+ *
+ * Conventions for every entry point:
+ *  - X is binary (every stored entry is 1) and is passed as indices only,
+ *    in both layouts: CSR (row_ptr int64[n+1], col_idx int32[nnz], columns
+ *    strictly increasing within a row) and CSC (col_ptr int64[p+1],
+ *    row_idx int32[nnz], rows strictly increasing within a column).  Both
+ *    must describe the same X; pcg_check_design verifies that.
+ *  - Every array pointer is a DEVICE pointer to memory owned by the caller
+ *    (the library never frees it and keeps no reference after the call
+ *    returns), except where a parameter is marked "host".
+ *  - Vectors are contiguous float64 unless stated.  Batched inputs are
+ *    chain-major: chain r's omega is omega[r*n .. r*n+n-1], and so on.
+ *  - Work is queued on the stream given to pcg_ctx_create (a cudaStream_t
+ *    passed as void*; NULL means the legacy default stream).  Each entry
+ *    point returns after its host outputs are written, which is the only
+ *    synchronisation it performs.
+ *  - Every entry point returns a pcg_status and never aborts the process.
+ *    On PCG_MAXITER the output holds the last iterate.  pcg_last_error gives
+ *    a one-line description of the most recent non-OK status of a context.
+ *  - Preconditions: omega_i > 0, lambda_j > 0, tau > 0 (PCG_BADARG is
+ *    returned for non-positive tau; non-finite results give
+ *    PCG_NONFINITE; a non-positive curvature s.Phi s gives PCG_BREAKDOWN).
+ */
+#ifndef PCG_BETA_H
+#define PCG_BETA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcg_ctx pcg_ctx;
+
+typedef enum pcg_status {
+    PCG_OK = 0,         /* converged under the stop rule */
+    PCG_MAXITER = 1,    /* max_iter reached first; output is the last iterate */
+    PCG_BREAKDOWN = 2,  /* s.Phi s <= 0 or rho <= 0 (Phi not SPD in floating point) */
+    PCG_NONFINITE = 3,  /* NaN or Inf in a CG scalar */
+    PCG_BADARG = 4,     /* invalid sizes, pointers, options or design */
+    PCG_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    PCG_CUDA = 6        /* a CUDA runtime call failed */
+} pcg_status;
+
+/* Arithmetic of the products u = Omega X s and v = X^T u. */
+enum {
+    PCG_PREC_FP64 = 0,          /* gathers and sums in float64 */
+    PCG_PREC_FP32_REFINED = 1,  /* float32 gathers and sums; CG scalars, beta and r in
+                                   float64; r = b - Phi beta recomputed in float64
+                                   every reliable_k iterations and before stopping */
+    PCG_PREC_FP32 = 2           /* float32 products, float64 scalars, no recomputation */
+};
+
+/* Stop rules.  With rho = r.(M^-1 r) = ||tau lambda (.) r||^2 (Sec. S4.2):
+ *   PCG_STOP_PAPER_RMS  stop when sqrt(rho / p) <= tol          (Eq. S2)
+ *   PCG_STOP_RELATIVE   stop when sqrt(rho / rho_0) <= tol      (rho_0 at beta_0 = 0) */
+enum { PCG_STOP_PAPER_RMS = 0, PCG_STOP_RELATIVE = 1 };
+
+/* Adjoint modes: gradient with b as an input, or with b built inside from (z, eta, delta). */
+enum { PCG_ADJ_SOLVE = 0, PCG_ADJ_DRAW = 1 };
+
+typedef struct pcg_csr {
+    int64_t n, p, nnz;
+    const int64_t *row_ptr;   /* device, n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    const int32_t *col_idx;   /* device, nnz entries in [0, p) */
+} pcg_csr;
+
+typedef struct pcg_csc {
+    int64_t n, p, nnz;
+    const int64_t *col_ptr;   /* device, p+1 entries, col_ptr[0] = 0, col_ptr[p] = nnz */
+    const int32_t *row_idx;   /* device, nnz entries in [0, n) */
+} pcg_csc;
+
+typedef struct pcg_options {
+    int precision;              /* PCG_PREC_*, default PCG_PREC_FP32_REFINED */
+    int reliable_k;             /* refined mode: also recompute r every k iterations (0: only
+                                   before stopping); default 50 */
+    int stop_rule;              /* PCG_STOP_*, default PCG_STOP_PAPER_RMS */
+    int use_graph;              /* 1 (default): the whole draw is one CUDA-graph launch whose
+                                   iteration loop is a device-side while node; 0: plain launches
+                                   with a host check every 8 iterations */
+    const char *autotune_cache; /* host path of a text file caching tuned launch shapes, or NULL */
+    int profile;                /* 1: time every kernel with CUDA events on the context stream
+                                   (forces plain launches); read with pcg_profile_entry */
+} pcg_options;
+
+/* Fills *opt with the defaults listed above. */
+pcg_status pcg_options_default(pcg_options *opt);
+
+/* Creates a context bound to the current CUDA device and to `stream`.  The
+ * context owns its workspace (grown on demand, freed by pcg_ctx_destroy) and
+ * its cached graphs.  A context must not be used by two host threads at once. */
+pcg_status pcg_ctx_create(pcg_ctx **ctx, const pcg_options *opt, void *stream);
+void pcg_ctx_destroy(pcg_ctx *ctx);
+const char *pcg_last_error(const pcg_ctx *ctx);
+
+/* Checks on the device that csr and csc are valid, agree in n, p and nnz and
+ * hold the same set of (i, j) entries; never dereferences a stored index.
+ * Returns PCG_OK or PCG_BADARG. */
+pcg_status pcg_check_design(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc);
+
+/*
+ * Right-hand side of Prop. 2.1, Eq. 2.3, in float64:
+ *   b_j = sum_{i : X_ij = 1} (omega_i z_i + sqrt(omega_i) eta_i) + delta_j / (tau lambda_j).
+ * omega, z, eta: n; lambda, delta: p; b (out): p.
+ */
+pcg_status pcg_build_rhs(pcg_ctx *ctx, const pcg_csc *X_csc, const double *omega, const double *z,
+                         const double *lambda, double tau, const double *eta,
+                         const double *delta, double *b);
+
+/*
+ * Matrix-free product of Sec. 1:  out = X^T (Omega (X v)) + tau^-2 Lambda^-2 v,
+ * with the products in the context's precision (float32 sums in the FP32
+ * modes, float64 otherwise) and the diagonal term in float64.
+ * v, out: p (float64); omega: n; lambda: p.
+ */
+pcg_status pcg_phi_mul(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                       const double *omega, const double *lambda, double tau,
+                       const double *v, double *out);
+
+/*
+ * One conditional draw: b by Eq. 2.3, then prior-preconditioned CG on Eq. 2.4.
+ * beta (out, p) receives the draw; *iters (host) the number of CG iterations
+ * (products Phi s); *resid (host) the final value of the stop quantity
+ * (sqrt(rho/p) or sqrt(rho/rho_0)).  max_iter >= 0; tol >= 0.
+ */
+pcg_status pcg_draw_beta(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                         const double *omega, const double *z, const double *lambda, double tau,
+                         const double *eta, const double *delta, double tol, int max_iter,
+                         double *beta, int *iters, double *resid);
+
+/*
+ * CG solve of Phi x = rhs (Eq. 2.4) for a given right-hand side (no Eq. 2.3
+ * step); same outputs as pcg_draw_beta.  Used by the adjoint, whose second
+ * solve Phi g = c shares Phi and the preconditioner.
+ */
+pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                     const double *omega, const double *lambda, double tau, const double *rhs,
+                     double tol, int max_iter, double *x, int *iters, double *resid);
+
+/*
+ * nrhs draws sharing X in one launch: each chain r has its own omega, z,
+ * lambda, tau, eta and delta (chain-major, see above; tau: device, nrhs) and
+ * runs its own CG scalars and stop test; the products are one sparse-times-
+ * dense-block pass per iteration over the RHS block.  beta (out): nrhs*p,
+ * chain-major.  iters, resid, status (host, nrhs each) receive each chain's
+ * result; the return value is the worst status.  1 <= nrhs <= 32.
+ */
+pcg_status pcg_draw_beta_batched(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                                 int nrhs, const double *omega, const double *z,
+                                 const double *lambda, const double *tau, const double *eta,
+                                 const double *delta, double tol, int max_iter, double *beta,
+                                 int *iters, double *resid, int *status);
+
+/* One independent problem of an uneven batch (all pointers device). */
+typedef struct pcg_problem {
+    pcg_csr X_csr;
+    pcg_csc X_csc;
+    const double *omega, *z, *lambda, *eta, *delta;
+    double tau;
+    double *beta;   /* out, p */
+} pcg_problem;
+
+/*
+ * Independent problems of uneven n and p, solved together by one persistent
+ * kernel launched from a CUDA graph: CTAs take (problem, tile) work items
+ * from a device queue; each problem advances its own CG with per-problem
+ * barriers whose waits are bounded (PCG_TIMEOUT if one gives up).
+ * probs: host array of nprob descriptors.  iters, resid, status: host, nprob.
+ */
+pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol,
+                                int max_iter, int *iters, double *resid, int *status);
+
+/*
+ * Adjoint of the draw for a loss L with dL/dbeta = grad_beta (p):
+ * one more prior-preconditioned CG solve Phi g = grad_beta, then
+ *   g_b        = g                                     (p)
+ *   g_omega    = -(X g) (.) (X beta)   [+ (X g) (.) (z + eta / (2 sqrt omega)) in DRAW mode]  (n)
+ *   g_loglambda = 2 d (.) g (.) beta    [- g (.) delta / (tau lambda) in DRAW mode]           (p)
+ *   *g_logtau (host) = sum_j g_loglambda_j
+ * with d = tau^-2 lambda^-2.  beta is the draw whose gradient is wanted
+ * (output of pcg_draw_beta).  In SOLVE mode z, eta, delta may be NULL.
+ * iters/resid (host) describe the adjoint solve.  Not in the paper: implicit
+ * differentiation of beta = Phi^-1 b with dPhi = X^T dOmega X + d(diag d).
+ */
+pcg_status pcg_adjoint(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                       const double *omega, const double *z, const double *lambda, double tau,
+                       const double *eta, const double *delta, const double *beta,
+                       const double *grad_beta, int mode, double tol, int max_iter,
+                       double *g_b, double *g_omega, double *g_loglambda, double *g_logtau,
+                       int *iters, double *resid);
+
+/*
+ * Measurement hooks (not in the paper; the paper times each linear-algebra
+ * operation separately in Sec. S7.2).  With opt.profile = 1 every kernel
+ * launch is bracketed by CUDA events on the context stream and accumulated
+ * per kernel name.  pcg_profile_count gives the number of distinct kernels
+ * seen; pcg_profile_entry(i) their name (valid until the next reset),
+ * total milliseconds and launch count; pcg_profile_reset clears them.
+ * pcg_last_kernel_launches gives the number of kernels the last entry point
+ * launched (every node of the CUDA graph that ran counts once per run).
+ */
+int pcg_profile_count(const pcg_ctx *ctx);
+pcg_status pcg_profile_entry(const pcg_ctx *ctx, int i, const char **name, double *total_ms,
+                             int64_t *launches);
+void pcg_profile_reset(pcg_ctx *ctx);
+int64_t pcg_last_kernel_launches(const pcg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCG_BETA_H */

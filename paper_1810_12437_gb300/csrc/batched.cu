@@ -1,0 +1,864 @@
+// Batched draws sharing X: R chains, each with its own omega, lambda, tau,
+// eta, delta and CG scalars, advanced together so that every iteration reads
+// the index streams of X once for the whole block of right-hand sides:
+//   U = Omega (.) (X S)           sparse times dense block (CSR pass)
+//   V = X^T U + D (.) S           (CSC pass), sigma_r = S_r . V_r
+// Vectors are interleaved [row][rhs] with the RHS count padded to RP (a power
+// of two >= 4), so one nonzero gathers RP contiguous float32 values as RP/4
+// float4 loads.  CG scalars, dot products, beta and r are float64; the
+// refined mode recomputes r = b - Phi beta in float64 (Sec. 2.4 recursion,
+// Eq. 2.3 right-hand sides, Eq. S2 stop rule per chain).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace pcg {
+
+struct BatchDesc {
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const double *omega, *z, *lambda, *tau, *eta, *delta;   // caller, chain-major
+    double *beta_out;                                     // caller, chain-major
+    int64_t n, p, nnz;
+    int R, RP;
+    double tol;
+    int max_iter, stop_rule, refined, reliable_k;
+};
+
+struct BatchWs {
+    double *b, *r, *s64, *v64, *beta, *m, *dg;   // p*RP each (interleaved)
+    float *s32;                                  // p*RP
+    void *u;                                     // n*RP doubles (w64, then u32 / u64)
+    double *om64;                                // n*RP
+    float *om32;                                 // n*RP
+    double *partials;                            // kMaxReduceBlocks * 32
+    unsigned int *counters;                      // 16
+    CgScalars *sc;                               // 32
+    int *flags;                                  // [0] all done, [1] any needs the recomputation
+    BatchDesc *desc;
+};
+
+// Grid reduction of NV values per block held in shared memory (vals), summed
+// in a fixed order.  Returns true in the last block, where sums[] holds the
+// totals.
+template <int NV>
+__device__ bool grid_reduce_arr(const double *vals, double *partials, unsigned int *counter,
+                                double *sums) {
+    __shared__ bool am_last;
+    __shared__ double tmp[256];
+    __syncthreads();
+    if (threadIdx.x < NV) partials[(size_t)blockIdx.x * NV + threadIdx.x] = vals[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    constexpr int NG = 256 / NV;
+    const int k = threadIdx.x % NV, grp = threadIdx.x / NV;
+    double a0 = 0.0, a1 = 0.0;
+    if (grp < NG && threadIdx.x < 256) {
+        unsigned b = grp;
+        for (; b + NG < gridDim.x; b += 2 * NG) {
+            a0 += __ldcg(partials + (size_t)b * NV + k);
+            a1 += __ldcg(partials + (size_t)(b + NG) * NV + k);
+        }
+        if (b < gridDim.x) a0 += __ldcg(partials + (size_t)b * NV + k);
+        tmp[threadIdx.x] = a0 + a1;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a = 0.0;
+        for (int g = 0; g < NG; ++g) a += tmp[g * NV + threadIdx.x];
+        sums[threadIdx.x] = a;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4shfl_xor(float4 a, int o) {
+    return make_float4(__shfl_xor_sync(kFull, a.x, o), __shfl_xor_sync(kFull, a.y, o),
+                       __shfl_xor_sync(kFull, a.z, o), __shfl_xor_sync(kFull, a.w, o));
+}
+__device__ __forceinline__ double2 d2add(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 d2shfl_xor(double2 a, int o) {
+    return make_double2(__shfl_xor_sync(kFull, a.x, o), __shfl_xor_sync(kFull, a.y, o));
+}
+
+// Sum over one CSR row / CSC column of the RP-wide float32 rows of x; lanes
+// are (slot, chunk) with RP/4 chunks of 4 values.  Valid in slot-0 lanes.
+template <int RP>
+__device__ __forceinline__ float4 block_row_sum_f32(const int32_t *__restrict__ idx, int64_t k0,
+                                                    int64_t k1, const float *__restrict__ x,
+                                                    bool active) {
+    constexpr int C = RP / 4, SL = 32 / C;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) {
+        int64_t k = k0 + slot;
+        for (; k + SL < k1; k += 2 * SL) {
+            const int32_t j0 = ld_stream(idx + k), j1 = ld_stream(idx + k + SL);
+            const float4 a0 = __ldg(reinterpret_cast<const float4 *>(x + (size_t)j0 * RP) + c);
+            const float4 a1 = __ldg(reinterpret_cast<const float4 *>(x + (size_t)j1 * RP) + c);
+            acc = f4add(acc, f4add(a0, a1));
+        }
+        if (k < k1) {
+            const int32_t j0 = ld_stream(idx + k);
+            acc = f4add(acc, __ldg(reinterpret_cast<const float4 *>(x + (size_t)j0 * RP) + c));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= C; o >>= 1) acc = f4add(acc, f4shfl_xor(acc, o));
+    return acc;
+}
+
+// Same in float64 with RP/2 chunks of 2 values.
+template <int RP>
+__device__ __forceinline__ double2 block_row_sum_f64(const int32_t *__restrict__ idx, int64_t k0,
+                                                     int64_t k1, const double *__restrict__ x,
+                                                     bool active) {
+    constexpr int C = RP / 2, SL = 32 / C;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C;
+    double2 acc = make_double2(0.0, 0.0);
+    if (active) {
+        for (int64_t k = k0 + slot; k < k1; k += SL) {
+            const int32_t j0 = ld_stream(idx + k);
+            acc = d2add(acc, __ldg(reinterpret_cast<const double2 *>(x + (size_t)j0 * RP) + c));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= C; o >>= 1) acc = d2add(acc, d2shfl_xor(acc, o));
+    return acc;
+}
+
+// ---- right-hand sides -----------------------------------------------------
+// w_{i,r} = omega z + sqrt(omega) eta; omega copies (float64 and float32),
+// interleaved; padding columns are zero.
+__global__ void k_b_prep(const BatchDesc *__restrict__ d, double *__restrict__ w,
+                         double *__restrict__ om64, float *__restrict__ om32) {
+    const int64_t n = d->n;
+    const int R = d->R, RP = d->RP;
+    const int64_t total = n * RP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / n);
+        const int64_t i = t - (int64_t)r * n;
+        double wv = 0.0, o = 0.0;
+        if (r < R) {
+            o = d->omega[t];
+            wv = o * d->z[t] + sqrt(o) * d->eta[t];
+        }
+        w[i * RP + r] = wv;
+        om64[i * RP + r] = o;
+        om32[i * RP + r] = (float)o;
+    }
+}
+
+// b = X^T w + delta / (tau lambda); m, d; beta = 0, r = b, s = m b, rho_0.
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_init(const BatchDesc *__restrict__ d,
+                                                const double *__restrict__ w, BatchWs ws) {
+    __shared__ double part[8][RP];
+    __shared__ double vals[RP];
+    __shared__ double sums[RP];
+    constexpr int C = RP / 2;
+    const int64_t p = d->p;
+    const int R = d->R;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C, warp_in_blk = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double rho[2] = {0.0, 0.0};
+    for (int64_t j = warp; j < p; j += nwarps) {
+        const double2 acc = block_row_sum_f64<RP>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], w, true);
+        if (slot == 0) {
+            const double a[2] = {acc.x, acc.y};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int r = 2 * c + q;
+                const size_t o = (size_t)j * RP + r;
+                double b = 0.0, m = 0.0, dg = 0.0;
+                if (r < R) {
+                    const double tau = d->tau[r], lam = d->lambda[(size_t)r * p + j];
+                    b = a[q] + d->delta[(size_t)r * p + j] / (tau * lam);
+                    m = prior_var(tau, lam);
+                    dg = prior_prec(tau, lam);
+                }
+                const double zz = m * b;
+                ws.b[o] = b;
+                ws.r[o] = b;
+                ws.m[o] = m;
+                ws.dg[o] = dg;
+                ws.s64[o] = zz;
+                ws.s32[o] = (float)zz;
+                ws.beta[o] = 0.0;
+                rho[q] += b * zz;
+            }
+        }
+    }
+    if (slot == 0) {
+        part[warp_in_blk][2 * c] = rho[0];
+        part[warp_in_blk][2 * c + 1] = rho[1];
+    }
+    __syncthreads();
+    if (threadIdx.x < RP) {
+        double a = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += part[w2][threadIdx.x];
+        vals[threadIdx.x] = a;
+    }
+    if (grid_reduce_arr<RP>(vals, ws.partials, ws.counters + 0, sums)) {
+        const int r = threadIdx.x;
+        if (r < R) {
+            CgScalars *sc = ws.sc + r;
+            const double r0 = sums[r];
+            sc->rho = r0;
+            sc->rho0 = r0;
+            sc->rho_prev = r0;
+            sc->sigma = sc->alpha = sc->gamma = 0.0;
+            sc->iter = 0;
+            sc->need_ru = 0;
+            sc->pending = 0;
+            sc->resid = stop_quantity(d->stop_rule, r0, r0, p);
+            if (!isfinite(r0)) { sc->status = PCG_NONFINITE; sc->done = 1; }
+            else if (stop_met(d->stop_rule, r0, r0, p, d->tol)) { sc->status = PCG_OK; sc->done = 1; }
+            else if (d->max_iter <= 0) { sc->status = PCG_MAXITER; sc->done = 1; }
+            else { sc->status = kRunning; sc->done = 0; }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int q = 0; q < R; ++q) all &= ws.sc[q].done ? 1 : 0;
+            ws.flags[0] = all;
+            ws.flags[1] = 0;
+            ws.flags[2] = 0;
+        }
+    }
+}
+
+// ---- per-iteration products -------------------------------------------------
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_csr(const BatchDesc *__restrict__ d,
+                                               const float *__restrict__ S,
+                                               const float *__restrict__ om,
+                                               float *__restrict__ U, const int *done_all) {
+    if (*(volatile const int *)done_all) return;
+    constexpr int C = RP / 4;
+    const int64_t n = d->n;
+    const int64_t *__restrict__ rp = d->row_ptr;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const float4 acc = block_row_sum_f32<RP>(d->col_idx, rp[i], rp[i + 1], S, true);
+        if (slot == 0) {
+            const float4 w = reinterpret_cast<const float4 *>(om + (size_t)i * RP)[c];
+            reinterpret_cast<float4 *>(U + (size_t)i * RP)[c] =
+                make_float4(acc.x * w.x, acc.y * w.y, acc.z * w.z, acc.w * w.w);
+        }
+    }
+}
+
+// float64 product on beta (refined mode): U64 = Omega (.) X beta
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_csr64(const BatchDesc *__restrict__ d,
+                                                 const double *__restrict__ B,
+                                                 const double *__restrict__ om,
+                                                 double *__restrict__ U, const int *flags) {
+    if (*(volatile const int *)&flags[0] || !*(volatile const int *)&flags[1]) return;
+    constexpr int C = RP / 2;
+    const int64_t n = d->n;
+    const int64_t *__restrict__ rp = d->row_ptr;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const double2 acc = block_row_sum_f64<RP>(d->col_idx, rp[i], rp[i + 1], B, true);
+        if (slot == 0) {
+            const double2 w = reinterpret_cast<const double2 *>(om + (size_t)i * RP)[c];
+            reinterpret_cast<double2 *>(U + (size_t)i * RP)[c] = make_double2(acc.x * w.x, acc.y * w.y);
+        }
+    }
+}
+
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_csc(const BatchDesc *__restrict__ d,
+                                               const float *__restrict__ U, BatchWs ws) {
+    __shared__ double part[8][RP];
+    __shared__ double vals[RP];
+    __shared__ double sums[RP];
+    if (*(volatile const int *)&ws.flags[0]) return;
+    constexpr int C = RP / 4;
+    const int64_t p = d->p;
+    const int R = d->R;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C, wib = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double sg[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j = warp; j < p; j += nwarps) {
+        const float4 acc = block_row_sum_f32<RP>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], U, true);
+        if (slot == 0) {
+            const float a[4] = {acc.x, acc.y, acc.z, acc.w};
+            const size_t o = (size_t)j * RP + 4 * c;
+            const double2 s01 = reinterpret_cast<const double2 *>(ws.s64 + o)[0];
+            const double2 s23 = reinterpret_cast<const double2 *>(ws.s64 + o)[1];
+            const double2 d01 = reinterpret_cast<const double2 *>(ws.dg + o)[0];
+            const double2 d23 = reinterpret_cast<const double2 *>(ws.dg + o)[1];
+            const double s[4] = {s01.x, s01.y, s23.x, s23.y};
+            const double dd[4] = {d01.x, d01.y, d23.x, d23.y};
+            double v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[q] = (double)a[q] + dd[q] * s[q];
+                sg[q] += s[q] * v[q];
+            }
+            reinterpret_cast<double2 *>(ws.v64 + o)[0] = make_double2(v[0], v[1]);
+            reinterpret_cast<double2 *>(ws.v64 + o)[1] = make_double2(v[2], v[3]);
+        }
+    }
+    if (slot == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) part[wib][4 * c + q] = sg[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < RP) {
+        double a = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += part[w2][threadIdx.x];
+        vals[threadIdx.x] = a;
+    }
+    if (grid_reduce_arr<RP>(vals, ws.partials, ws.counters + 1, sums)) {
+        const int r = threadIdx.x;
+        if (r < R) {
+            CgScalars *sc = ws.sc + r;
+            if (!sc->done) {
+                const double sigma = sums[r];
+                sc->sigma = sigma;
+                if (!isfinite(sigma)) { sc->status = PCG_NONFINITE; sc->done = 1; }
+                else if (!(sigma > 0.0) || !(sc->rho > 0.0)) { sc->status = PCG_BREAKDOWN; sc->done = 1; }
+                else sc->alpha = sc->rho / sigma;
+            }
+        }
+    }
+}
+
+// beta += alpha s, r -= alpha v, rho' per chain; stop tests and bookkeeping.
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_update(const BatchDesc *__restrict__ d, BatchWs ws,
+                                                  cudaGraphConditionalHandle h_ru, int use_cond) {
+    __shared__ double part[8][RP];
+    __shared__ double vals[RP];
+    __shared__ double sums[RP];
+    if (*(volatile const int *)&ws.flags[0]) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_ru, 0);
+        return;
+    }
+    const int64_t p = d->p;
+    const int R = d->R;
+    const int r = threadIdx.x % RP;          // fixed per thread: the stride is a multiple of RP
+    const bool live = r < R && !ws.sc[r].done;
+    const double alpha = live ? ws.sc[r].alpha : 0.0;
+    double rho = 0.0;
+    const int64_t total = p * RP;
+    if (live) {
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const double bj = ws.beta[t] + alpha * ws.s64[t];
+            const double rj = ws.r[t] - alpha * ws.v64[t];
+            ws.beta[t] = bj;
+            ws.r[t] = rj;
+            rho += rj * (ws.m[t] * rj);
+        }
+    }
+    // lanes with equal r: xor over the lane bits above RP
+#pragma unroll
+    for (int o = 16; o >= RP; o >>= 1) rho += __shfl_xor_sync(kFull, rho, o);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (RP <= 32 && lane < RP) part[wib][lane] = rho;
+    __syncthreads();
+    if (threadIdx.x < RP) {
+        double a = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += part[w2][threadIdx.x];
+        vals[threadIdx.x] = a;
+    }
+    if (grid_reduce_arr<RP>(vals, ws.partials, ws.counters + 2, sums)) {
+        const int q = threadIdx.x;
+        if (q < R) {
+            CgScalars *sc = ws.sc + q;
+            if (!sc->done) {
+                const double rn = sums[q];
+                sc->iter += 1;
+                if (!isfinite(rn)) {
+                    sc->status = PCG_NONFINITE;
+                    sc->done = 1;
+                    sc->need_ru = 0;
+                } else {
+                    const bool conv = stop_met(d->stop_rule, rn, sc->rho0, p, d->tol);
+                    sc->rho_prev = sc->rho;
+                    sc->rho = rn;
+                    sc->gamma = rn / sc->rho_prev;
+                    sc->resid = stop_quantity(d->stop_rule, rn, sc->rho0, p);
+                    if (d->refined) {
+                        const bool periodic = d->reliable_k > 0 && (sc->iter % d->reliable_k) == 0;
+                        sc->pending = conv ? 1 : 0;
+                        sc->need_ru = (conv || periodic) ? 1 : 0;
+                        if (!conv && sc->iter >= d->max_iter) {
+                            sc->status = PCG_MAXITER;
+                            sc->done = 1;
+                            sc->need_ru = 0;
+                        }
+                    } else if (conv) {
+                        sc->status = PCG_OK;
+                        sc->done = 1;
+                    } else if (sc->iter >= d->max_iter) {
+                        sc->status = PCG_MAXITER;
+                        sc->done = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1, any = 0;
+            for (int k = 0; k < R; ++k) {
+                all &= ws.sc[k].done ? 1 : 0;
+                any |= (ws.sc[k].need_ru && !ws.sc[k].done) ? 1 : 0;
+            }
+            ws.flags[0] = all;
+            ws.flags[1] = any;
+            if (any && !all) ws.flags[2] += 1;
+            if (use_cond) cudaGraphSetConditional(h_ru, (any && !all) ? 1u : 0u);
+        }
+    }
+}
+
+// r = b - (X^T U64 + d beta) for the chains that asked for it.
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_true_resid(const BatchDesc *__restrict__ d,
+                                                      const double *__restrict__ U, BatchWs ws) {
+    __shared__ double part[8][RP];
+    __shared__ double vals[RP];
+    __shared__ double sums[RP];
+    if (*(volatile const int *)&ws.flags[0] || !*(volatile const int *)&ws.flags[1]) return;
+    constexpr int C = RP / 2;
+    const int64_t p = d->p;
+    const int R = d->R;
+    const int lane = threadIdx.x & 31, c = lane % C, slot = lane / C, wib = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool want[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = 2 * c + q;
+        want[q] = r < R && ws.sc[r].need_ru && !ws.sc[r].done;
+    }
+    double rho[2] = {0.0, 0.0};
+    for (int64_t j = warp; j < p; j += nwarps) {
+        const double2 acc = block_row_sum_f64<RP>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], U, true);
+        if (slot == 0) {
+            const double a[2] = {acc.x, acc.y};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!want[q]) continue;
+                const size_t o = (size_t)j * RP + 2 * c + q;
+                const double rj = ws.b[o] - (a[q] + ws.dg[o] * ws.beta[o]);
+                ws.r[o] = rj;
+                rho[q] += rj * (ws.m[o] * rj);
+            }
+        }
+    }
+    if (slot == 0) {
+        part[wib][2 * c] = rho[0];
+        part[wib][2 * c + 1] = rho[1];
+    }
+    __syncthreads();
+    if (threadIdx.x < RP) {
+        double a = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += part[w2][threadIdx.x];
+        vals[threadIdx.x] = a;
+    }
+    if (grid_reduce_arr<RP>(vals, ws.partials, ws.counters + 3, sums)) {
+        const int q = threadIdx.x;
+        if (q < R) {
+            CgScalars *sc = ws.sc + q;
+            if (sc->need_ru && !sc->done) {
+                const double rt = sums[q];
+                sc->need_ru = 0;
+                if (!isfinite(rt)) {
+                    sc->status = PCG_NONFINITE;
+                    sc->done = 1;
+                } else {
+                    sc->rho = rt;
+                    sc->gamma = rt / sc->rho_prev;
+                    sc->resid = stop_quantity(d->stop_rule, rt, sc->rho0, p);
+                    if (sc->pending) {
+                        if (stop_met(d->stop_rule, rt, sc->rho0, p, d->tol)) {
+                            sc->status = PCG_OK;
+                            sc->done = 1;
+                        } else {
+                            sc->pending = 0;
+                            if (sc->iter >= d->max_iter) { sc->status = PCG_MAXITER; sc->done = 1; }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int k = 0; k < R; ++k) all &= ws.sc[k].done ? 1 : 0;
+            ws.flags[0] = all;
+            ws.flags[1] = 0;
+        }
+    }
+}
+
+// s = m r + gamma s for live chains; sets the while condition.
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d, BatchWs ws,
+                                                cudaGraphConditionalHandle h_while, int use_cond) {
+    const int all = *(volatile const int *)&ws.flags[0];
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_while, all ? 0u : 1u);
+    if (all) return;
+    const int r = threadIdx.x % RP;
+    if (r >= d->R || ws.sc[r].done) return;
+    const double gamma = ws.sc[r].gamma;
+    const int64_t total = d->p * RP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double s = ws.m[t] * ws.r[t] + gamma * ws.s64[t];
+        ws.s64[t] = s;
+        ws.s32[t] = (float)s;
+    }
+}
+
+// interleaved beta -> caller's chain-major beta
+__global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restrict__ beta) {
+    const int64_t p = d->p;
+    const int R = d->R, RP = d->RP;
+    const int64_t total = p * R;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / p);
+        const int64_t j = t - (int64_t)r * p;
+        d->beta_out[t] = beta[j * RP + r];
+    }
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+
+static cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps,
+                            size_t ndeps, void *func, int grid, int block, void **args) {
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+struct BatchKernels {
+    void *init, *csr, *csr64, *csc, *update, *true_resid, *sdir;
+};
+
+template <int RP>
+static BatchKernels batch_kernels() {
+    return {(void *)k_b_init<RP>, (void *)k_b_csr<RP>, (void *)k_b_csr64<RP>, (void *)k_b_csc<RP>,
+            (void *)k_b_update<RP>, (void *)k_b_true_resid<RP>, (void *)k_b_sdir<RP>};
+}
+
+static BatchKernels kernels_for(int RP) {
+    switch (RP) {
+        case 4: return batch_kernels<4>();
+        case 8: return batch_kernels<8>();
+        case 16: return batch_kernels<16>();
+        default: return batch_kernels<32>();
+    }
+}
+
+struct BatchNodeArgs {
+    const BatchDesc *d;
+    BatchWs ws;
+    double *w64;
+    double *om64;
+    float *om32;
+    const float *s32;
+    float *u32;
+    const double *u64c;
+    double *u64;
+    const double *beta;
+    const int *flag0;
+    const int *flags;
+    cudaGraphConditionalHandle h_while, h_ru;
+    int one, use_ru;
+};
+
+static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, bool refined,
+                                    cudaGraphExec_t *out) {
+    const BatchKernels K = kernels_for(RP);
+    const int grid = grid_for(ctx, 256, 8);
+    const int gvec = grid_for(ctx, 256, 4);
+    BatchNodeArgs A{};
+    A.d = ws.desc;
+    A.ws = ws;
+    A.w64 = (double *)ws.u;
+    A.om64 = ws.om64;
+    A.om32 = ws.om32;
+    A.s32 = ws.s32;
+    A.u32 = (float *)ws.u;
+    A.u64 = (double *)ws.u;
+    A.u64c = (const double *)ws.u;
+    A.beta = ws.beta;
+    A.flag0 = ws.flags;
+    A.flags = ws.flags;
+    A.one = 1;
+    A.use_ru = refined ? 1 : 0;
+    cudaGraph_t g = nullptr;
+    PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
+    cudaError_t e;
+    cudaGraphNode_t n_prep, n_init, n_while, n_csr, n_csc, n_upd, n_if, n_sdir, n_r1, n_r2, n_out;
+    {
+        void *a[] = {&A.d, &A.w64, &A.om64, &A.om32};
+        e = add_node(g, &n_prep, nullptr, 0, (void *)k_b_prep, grid, 256, a);
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.w64, &A.ws};
+        e = add_node(g, &n_init, &n_prep, 1, K.init, grid, 256, a);
+    }
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&A.h_while, g, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = A.h_while;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.s32, &A.om32, &A.u32, &A.flag0};
+        e = add_node(body, &n_csr, nullptr, 0, K.csr, grid, 256, a);
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.u32, &A.ws};
+        e = add_node(body, &n_csc, &n_csr, 1, K.csc, grid, 256, a);
+    }
+    if (e == cudaSuccess && refined) e = cudaGraphConditionalHandleCreate(&A.h_ru, body, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.ws, &A.h_ru, &A.use_ru};
+        e = add_node(body, &n_upd, &n_csc, 1, K.update, gvec, 256, a);
+    }
+    cudaGraphNode_t last = n_upd;
+    if (e == cudaSuccess && refined) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = A.h_ru;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_if, body, &n_upd, nullptr, 1, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t ifb = cp.conditional.phGraph_out[0];
+            void *a1[] = {&A.d, &A.beta, &A.om64, &A.u64, &A.flags};
+            e = add_node(ifb, &n_r1, nullptr, 0, K.csr64, grid, 256, a1);
+            if (e == cudaSuccess) {
+                void *a2[] = {&A.d, &A.u64c, &A.ws};
+                e = add_node(ifb, &n_r2, &n_r1, 1, K.true_resid, grid, 256, a2);
+            }
+            last = n_if;
+        }
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.ws, &A.h_while, &A.one};
+        e = add_node(body, &n_sdir, &last, 1, K.sdir, gvec, 256, a);
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&A.d, &A.beta};
+        e = add_node(g, &n_out, &n_while, 1, (void *)k_b_out, gvec, 256, a);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "building the batched graph");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "instantiating the batched graph");
+    *out = exec;
+    return PCG_OK;
+}
+
+template <int RP>
+static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refined, int grid, int gvec) {
+    cudaStream_t st = ctx->stream;
+    PCG_PROF(ctx, "b_csr_f32", k_b_csr<RP><<<grid, 256, 0, st>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, ws.flags));
+    PCG_PROF(ctx, "b_csc_f32", k_b_csc<RP><<<grid, 256, 0, st>>>(ws.desc, (const float *)ws.u, ws));
+    PCG_PROF(ctx, "b_update", k_b_update<RP><<<gvec, 256, 0, st>>>(ws.desc, ws, 0, 0));
+    if (refined) {
+        PCG_PROF(ctx, "b_ru_csr_f64", k_b_csr64<RP><<<grid, 256, 0, st>>>(ws.desc, ws.beta, ws.om64, (double *)ws.u, ws.flags));
+        PCG_PROF(ctx, "b_ru_true_resid", k_b_true_resid<RP><<<grid, 256, 0, st>>>(ws.desc, (const double *)ws.u, ws));
+    }
+    PCG_PROF(ctx, "b_sdir", k_b_sdir<RP><<<gvec, 256, 0, st>>>(ws.desc, ws, 0, 0));
+}
+
+template <int RP>
+static void launch_batch_plain_init(pcg_ctx *ctx, const BatchWs &ws, int grid) {
+    PCG_PROF(ctx, "b_prep", k_b_prep<<<grid, 256, 0, ctx->stream>>>(ws.desc, (double *)ws.u, ws.om64, ws.om32));
+    PCG_PROF(ctx, "b_init", k_b_init<RP><<<grid, 256, 0, ctx->stream>>>(ws.desc, (const double *)ws.u, ws));
+}
+
+pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int nrhs,
+                       const double *omega, const double *z, const double *lambda,
+                       const double *tau, const double *eta, const double *delta, double tol,
+                       int max_iter, double *beta, int *iters, double *resid, int *status) {
+    int RP = 4;
+    while (RP < nrhs) RP *= 2;
+    const int64_t n = std::max<int64_t>(Xr->n, 1), p = std::max<int64_t>(Xr->p, 1);
+    const size_t vp = sizeof(double) * (size_t)p * RP;
+    const size_t al = 256;
+    auto up = [&](size_t x) { return (x + al - 1) / al * al; };
+    // one block for the p-sized vectors and the small state
+    const size_t total_p = 7 * up(vp) + up(sizeof(float) * (size_t)p * RP) +
+                           up(sizeof(double) * kMaxReduceBlocks * 32) + up(64 * sizeof(unsigned)) +
+                           up(sizeof(CgScalars) * kMaxBatch) + up(64) + up(sizeof(BatchDesc));
+    cudaError_t e;
+    char *bp = (char *)grow(ctx, "batch_p", total_p, &e);
+    if (!bp) return cuda_error(ctx, e, "allocating the batched workspace");
+    void *bu = grow(ctx, "batch_u", sizeof(double) * (size_t)n * RP, &e);
+    if (!bu) return cuda_error(ctx, e, "allocating the batched workspace");
+    double *bom64 = (double *)grow(ctx, "batch_om64", sizeof(double) * (size_t)n * RP, &e);
+    if (!bom64) return cuda_error(ctx, e, "allocating the batched workspace");
+    float *bom32 = (float *)grow(ctx, "batch_om32", sizeof(float) * (size_t)n * RP, &e);
+    if (!bom32) return cuda_error(ctx, e, "allocating the batched workspace");
+    BatchWs ws{};
+    size_t off = 0;
+    auto take = [&](size_t sz) { char *q = bp + off; off += up(sz); return q; };
+    ws.b = (double *)take(vp);
+    ws.r = (double *)take(vp);
+    ws.s64 = (double *)take(vp);
+    ws.v64 = (double *)take(vp);
+    ws.beta = (double *)take(vp);
+    ws.m = (double *)take(vp);
+    ws.dg = (double *)take(vp);
+    ws.s32 = (float *)take(sizeof(float) * (size_t)p * RP);
+    ws.partials = (double *)take(sizeof(double) * kMaxReduceBlocks * 32);
+    ws.counters = (unsigned *)take(64 * sizeof(unsigned));
+    ws.sc = (CgScalars *)take(sizeof(CgScalars) * kMaxBatch);
+    ws.flags = (int *)take(64);
+    ws.desc = (BatchDesc *)take(sizeof(BatchDesc));
+    ws.u = bu;
+    ws.om64 = bom64;
+    ws.om32 = bom32;
+    // counters must start at zero; the rest is written before it is read
+    PCG_CUDA_TRY(ctx, cudaMemsetAsync(ws.counters, 0, 64 * sizeof(unsigned), ctx->stream));
+
+    BatchDesc *hd = (BatchDesc *)grow_host(ctx, "batch_desc", sizeof(BatchDesc), &e);
+    CgScalars *hsc = (CgScalars *)grow_host(ctx, "batch_sc", sizeof(CgScalars) * kMaxBatch, &e);
+    if (!hd || !hsc) return cuda_error(ctx, e, "allocating pinned staging");
+    BatchDesc d{};
+    d.row_ptr = Xr->row_ptr;
+    d.col_idx = Xr->col_idx;
+    d.col_ptr = Xc->col_ptr;
+    d.row_idx = Xc->row_idx;
+    d.omega = omega;
+    d.z = z;
+    d.lambda = lambda;
+    d.tau = tau;
+    d.eta = eta;
+    d.delta = delta;
+    d.beta_out = beta;
+    d.n = Xr->n;
+    d.p = Xr->p;
+    d.nnz = Xr->nnz;
+    d.R = nrhs;
+    d.RP = RP;
+    d.tol = tol;
+    d.max_iter = max_iter;
+    d.stop_rule = ctx->opt.stop_rule;
+    d.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
+    d.reliable_k = ctx->opt.reliable_k;
+    *hd = d;
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->opt.precision == PCG_PREC_FP64)
+        return set_error(ctx, PCG_BADARG, "the batched path computes its products in float32: use PCG_PREC_FP32_REFINED or PCG_PREC_FP32");
+    const bool refined = d.refined != 0;
+    const int grid = grid_for(ctx, 256, 8), gvec = grid_for(ctx, 256, 4);
+    int *hflags_g = (int *)grow_host(ctx, "batch_flags_g", 64, &e);
+    if (!hflags_g) return cuda_error(ctx, e, "allocating pinned staging");
+    if (ctx->opt.use_graph && !ctx->opt.profile) {
+        char key[160];
+        snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p", RP, (int)refined, grid, gvec,
+                 (void *)bp, bu, (void *)bom64, (void *)bom32);
+        auto it = ctx->named_graphs.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (it == ctx->named_graphs.end()) {
+            pcg_status st = build_batch_graph(ctx, ws, RP, refined, &exec);
+            if (st != PCG_OK) return st;
+            ctx->named_graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+        PCG_CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags_g, ws.flags, 64, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        // graph nodes that ran: prep, init and the output transpose, 4 per loop
+        // trip (at least one), 2 per float64 recomputation of r
+        int trips = 1;
+        for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
+        ctx->last_launches += 3 + 4 * (int64_t)trips + 2 * (int64_t)hflags_g[2];
+    } else {
+        switch (RP) {
+            case 4: launch_batch_plain_init<4>(ctx, ws, grid); break;
+            case 8: launch_batch_plain_init<8>(ctx, ws, grid); break;
+            case 16: launch_batch_plain_init<16>(ctx, ws, grid); break;
+            default: launch_batch_plain_init<32>(ctx, ws, grid); break;
+        }
+        int *hflags = (int *)grow_host(ctx, "batch_flags", 64, &e);
+        if (!hflags) return cuda_error(ctx, e, "allocating pinned staging");
+        for (int it = 0;; it += 8) {
+            for (int k = 0; k < 8; ++k) {
+                switch (RP) {
+                    case 4: launch_batch_plain_iter<4>(ctx, ws, refined, grid, gvec); break;
+                    case 8: launch_batch_plain_iter<8>(ctx, ws, refined, grid, gvec); break;
+                    case 16: launch_batch_plain_iter<16>(ctx, ws, refined, grid, gvec); break;
+                    default: launch_batch_plain_iter<32>(ctx, ws, refined, grid, gvec); break;
+                }
+            }
+            PCG_CUDA_TRY(ctx, cudaGetLastError());
+            PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, 64, cudaMemcpyDeviceToHost, ctx->stream));
+            PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            prof_collect(ctx);
+            if (hflags[0]) break;
+            if (it > max_iter + 16) return set_error(ctx, PCG_TIMEOUT, "host loop ran past max_iter");
+        }
+        PCG_PROF(ctx, "b_out", k_b_out<<<gvec, 256, 0, ctx->stream>>>(ws.desc, ws.beta));
+        PCG_CUDA_TRY(ctx, cudaGetLastError());
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        prof_collect(ctx);
+    }
+    pcg_status worst = PCG_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        iters[r] = hsc[r].iter;
+        resid[r] = hsc[r].resid;
+        status[r] = hsc[r].status == kRunning ? PCG_TIMEOUT : hsc[r].status;
+        if (status[r] > worst) worst = (pcg_status)status[r];
+    }
+    if (worst != PCG_OK) return set_error(ctx, worst, "at least one chain did not converge (see status[])");
+    return PCG_OK;
+}
+
+}  // namespace pcg

@@ -1,0 +1,795 @@
+// Single right-hand-side path: Prop. 2.1 right-hand side (Eq. 2.3) and
+// prior-preconditioned CG (Sec. 2.4, Algorithm S1, stop rule Eq. S2) on
+// Phi beta = b (Eq. 2.4), with Phi applied matrix-free as
+// u = Omega (X s) (CSR pass) and v = X^T u + tau^-2 Lambda^-2 s (CSC pass).
+//
+// Kernels of one CG iteration (device-side while loop of a CUDA graph):
+//   k_csr        u_i = omega_i sum_{j in row i} s_j
+//   k_csc        v_j = sum_{i in col j} u_i + d_j s_j,   sigma = s.v,  alpha = rho/sigma
+//   k_update     beta += alpha s, r -= alpha v, rho' = r.(m r); stop test; gamma
+//   [if need_ru] k_csr on beta in float64, then k_true_resid: r = b - Phi beta,
+//                rho = r.(m r)   (reliable update of the refined mode)
+//   k_sdir       s = m r + gamma s   (and its float32 copy for the next gathers)
+// with d = tau^-2 lambda^-2 and m = tau^2 lambda^2.  Every dot product and
+// CG scalar is float64; the grid reductions are deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace pcg {
+
+// ---------------------------------------------------------------------------
+// lane-partial gather-sum of one CSR row / CSC column by a group of G lanes;
+// the caller combines the group with group_sum outside any divergent branch.
+// ---------------------------------------------------------------------------
+template <int G, typename T>
+__device__ __forceinline__ T segment_partial(const int32_t *__restrict__ idx, int64_t k0,
+                                                int64_t k1, const T *__restrict__ x, int lane) {
+    T acc = T(0);
+    int64_t k = k0 + lane;
+    for (; k + 3 * G < k1; k += 4 * G) {
+        const int32_t j0 = ld_stream(idx + k), j1 = ld_stream(idx + k + G);
+        const int32_t j2 = ld_stream(idx + k + 2 * G), j3 = ld_stream(idx + k + 3 * G);
+        const T a0 = ld_gather(x + j0), a1 = ld_gather(x + j1);
+        const T a2 = ld_gather(x + j2), a3 = ld_gather(x + j3);
+        acc += (a0 + a1) + (a2 + a3);
+    }
+    for (; k < k1; k += G) acc += ld_gather(x + ld_stream(idx + k));
+    return acc;
+}
+
+__device__ __forceinline__ bool gate_closed(const int *done, const int *need) {
+    return *(volatile const int *)done || (need && !*(volatile const int *)need);
+}
+
+// ---------------------------------------------------------------------------
+// a1: w_i = omega_i z_i + sqrt(omega_i) eta_i (float64), and the float32 copy
+// of omega used by the float32 products.
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_w(const DrawDesc *__restrict__ d, double *__restrict__ w,
+                        float *__restrict__ om32, int want_w, int want_om32) {
+    const int64_t n = d->n;
+    const double *__restrict__ om = d->omega;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double o = om[i];
+        if (want_w) w[i] = o * d->z[i] + sqrt(o) * d->eta[i];
+        if (want_om32) om32[i] = (float)o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a1 + a2: b_j = sum_{i in col j} w_i + delta_j / (tau lambda_j)  (or the given
+// right-hand side), then beta = 0, r = b, z = m b, s = z, rho_0 = r.z.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d,
+                                                  const double *__restrict__ w, SingleWs ws) {
+    __shared__ double red[32];
+    __shared__ double sums[1];
+    const int64_t p = d->p;
+    const double tau = d->tau;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    double rho = 0.0;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        double acc = 0.0;
+        if (d->rhs == nullptr && j < p)
+            acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], w, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) {
+            const double lam = d->lambda[j];
+            const double b = d->rhs ? d->rhs[j] : acc + d->delta[j] / (tau * lam);
+            const double z = prior_var(tau, lam) * b;
+            ws.b[j] = b;
+            ws.r[j] = b;
+            ws.s64[j] = z;
+            ws.s32[j] = (float)z;
+            d->beta[j] = 0.0;
+            rho += b * z;
+        }
+    }
+    const double tot = block_sum(rho, red);
+    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 0, sums, red) && threadIdx.x == 0) {
+        CgScalars *sc = ws.sc;
+        const double r0 = sums[0];
+        sc->rho = r0;
+        sc->rho0 = r0;
+        sc->rho_prev = r0;
+        sc->sigma = 0.0;
+        sc->alpha = 0.0;
+        sc->gamma = 0.0;
+        sc->iter = 0;
+        sc->need_ru = 0;
+        sc->pending = 0;
+        sc->ru_trips = 0;
+        sc->resid = stop_quantity(d->stop_rule, r0, r0, p);
+        if (!isfinite(r0)) {
+            sc->status = PCG_NONFINITE;
+            sc->done = 1;
+        } else if (stop_met(d->stop_rule, r0, r0, p, d->tol)) {
+            sc->status = PCG_OK;
+            sc->done = 1;
+        } else if (d->max_iter <= 0) {
+            sc->status = PCG_MAXITER;
+            sc->done = 1;
+        } else {
+            sc->status = kRunning;
+            sc->done = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3: u_i = omega_i sum_{j in row i} s_j   (T = float: float32 gathers and sums)
+// ---------------------------------------------------------------------------
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_csr(const DrawDesc *__restrict__ d,
+                                             const T *__restrict__ s, const T *__restrict__ om,
+                                             T *__restrict__ u, const int *done, const int *need) {
+    if (gate_closed(done, need)) return;
+    // float64 callers may pass NULL to read beta (s) or omega (om) from the
+    // descriptor, so that cached graphs hold no caller pointer.
+    const T *__restrict__ sv = s ? s : (const T *)d->beta;
+    const T *__restrict__ omv = om ? om : (const T *)d->omega;
+    const int64_t n = d->n;
+    const int64_t *__restrict__ rp = d->row_ptr;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    for (int64_t base = warp * gpw; base < n; base += nwarps * gpw) {
+        const int64_t i = base + sub;
+        T acc = T(0);
+        if (i < n)
+            acc = segment_partial<G, T>(d->col_idx, rp[i], rp[i + 1], sv, lane);
+        acc = group_sum<G>(acc);
+        if (i < n && lane == 0) u[i] = omv[i] * acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4 + a5: v_j = sum_{i in col j} u_i + d_j s_j (float64 out), sigma = s.v,
+// alpha = rho / sigma.  With `out` set (pcg_phi_mul) it only writes out = v.
+// ---------------------------------------------------------------------------
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_csc(const DrawDesc *__restrict__ d,
+                                             const T *__restrict__ u, const double *__restrict__ sv,
+                                             double *__restrict__ out, SingleWs ws, int reduce) {
+    __shared__ double red[32];
+    __shared__ double sums[1];
+    if (reduce && *(volatile const int *)&ws.sc->done) return;
+    const int64_t p = d->p;
+    const double tau = d->tau;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    double sig = 0.0;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        T acc = T(0);
+        if (j < p)
+            acc = segment_partial<G, T>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], u, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) {
+            const double sj = sv[j];
+            const double v = (double)acc + prior_prec(tau, d->lambda[j]) * sj;
+            out[j] = v;
+            sig += sj * v;
+        }
+    }
+    if (!reduce) return;
+    const double tot = block_sum(sig, red);
+    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 1, sums, red) && threadIdx.x == 0) {
+        CgScalars *sc = ws.sc;
+        const double sigma = sums[0];
+        sc->sigma = sigma;
+        if (!isfinite(sigma)) {
+            sc->status = PCG_NONFINITE;
+            sc->done = 1;
+        } else if (!(sigma > 0.0) || !(sc->rho > 0.0)) {
+            sc->status = PCG_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rho / sigma;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6 + a7: beta += alpha s; r -= alpha v; rho' = r.(m r); stop test; gamma.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_update(const DrawDesc *__restrict__ d, SingleWs ws,
+                                                cudaGraphConditionalHandle h_ru, int use_cond) {
+    __shared__ double red[32];
+    __shared__ double sums[1];
+    CgScalars *sc = ws.sc;
+    if (*(volatile const int *)&sc->done) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_ru, 0);
+        return;
+    }
+    const int64_t p = d->p;
+    const double tau = d->tau;
+    const double alpha = sc->alpha;
+    double rho = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double bj = d->beta[j] + alpha * ws.s64[j];
+        const double rj = ws.r[j] - alpha * ws.v64[j];
+        d->beta[j] = bj;
+        ws.r[j] = rj;
+        rho += rj * (prior_var(tau, d->lambda[j]) * rj);
+    }
+    const double tot = block_sum(rho, red);
+    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 2, sums, red) && threadIdx.x == 0) {
+        const double rn = sums[0];
+        sc->iter += 1;
+        if (!isfinite(rn)) {
+            sc->status = PCG_NONFINITE;
+            sc->done = 1;
+            sc->need_ru = 0;
+        } else {
+            const bool conv = stop_met(d->stop_rule, rn, sc->rho0, p, d->tol);
+            sc->rho_prev = sc->rho;
+            sc->rho = rn;
+            sc->gamma = rn / sc->rho_prev;
+            sc->resid = stop_quantity(d->stop_rule, rn, sc->rho0, p);
+            if (d->refined) {
+                const bool periodic = d->reliable_k > 0 && (sc->iter % d->reliable_k) == 0;
+                sc->pending = conv ? 1 : 0;
+                sc->need_ru = (conv || periodic) ? 1 : 0;
+                if (!conv && sc->iter >= d->max_iter) {
+                    sc->status = PCG_MAXITER;
+                    sc->done = 1;
+                    sc->need_ru = 0;
+                }
+            } else if (conv) {
+                sc->status = PCG_OK;
+                sc->done = 1;
+            } else if (sc->iter >= d->max_iter) {
+                sc->status = PCG_MAXITER;
+                sc->done = 1;
+            }
+        }
+        if (sc->need_ru && !sc->done) sc->ru_trips += 1;
+        if (use_cond) cudaGraphSetConditional(h_ru, (sc->need_ru && !sc->done) ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a8 (refined mode): r = b - (X^T u64 + d beta) with u64 = Omega X beta in
+// float64; rho = r.(m r) replaces the recursion's value.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__ d,
+                                                    const double *__restrict__ u64, SingleWs ws,
+                                                    int gated) {
+    __shared__ double red[32];
+    __shared__ double sums[1];
+    CgScalars *sc = ws.sc;
+    if (gated && gate_closed(&sc->done, &sc->need_ru)) return;
+    const int64_t p = d->p;
+    const double tau = d->tau;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    double rho = 0.0;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        double acc = 0.0;
+        if (j < p)
+            acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], u64, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) {
+            const double lam = d->lambda[j];
+            const double bj = d->beta[j];
+            const double rj = ws.b[j] - (acc + prior_prec(tau, lam) * bj);
+            ws.r[j] = rj;
+            rho += rj * (prior_var(tau, lam) * rj);
+        }
+    }
+    const double tot = block_sum(rho, red);
+    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 3, sums, red) && threadIdx.x == 0) {
+        const double rt = sums[0];
+        sc->need_ru = 0;
+        if (!isfinite(rt)) {
+            sc->status = PCG_NONFINITE;
+            sc->done = 1;
+        } else {
+            sc->rho = rt;
+            sc->gamma = rt / sc->rho_prev;
+            sc->resid = stop_quantity(d->stop_rule, rt, sc->rho0, p);
+            if (sc->pending) {
+                if (stop_met(d->stop_rule, rt, sc->rho0, p, d->tol)) {
+                    sc->status = PCG_OK;
+                    sc->done = 1;
+                } else {
+                    sc->pending = 0;
+                    if (sc->iter >= d->max_iter) {
+                        sc->status = PCG_MAXITER;
+                        sc->done = 1;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// s = m r + gamma s (float64 master and float32 gather copy); sets the while
+// condition of the graph to "not done".
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sdir(const DrawDesc *__restrict__ d, SingleWs ws,
+                                              cudaGraphConditionalHandle h_while, int use_cond) {
+    CgScalars *sc = ws.sc;
+    const int done = *(volatile const int *)&sc->done;
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+        cudaGraphSetConditional(h_while, done ? 0u : 1u);
+    if (done) return;
+    const int64_t p = d->p;
+    const double tau = d->tau;
+    const double gamma = sc->gamma;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double s = prior_var(tau, d->lambda[j]) * ws.r[j] + gamma * ws.s64[j];
+        ws.s64[j] = s;
+        ws.s32[j] = (float)s;
+    }
+}
+
+// v (float64) -> float32 copy (pcg_phi_mul in the float32 modes)
+__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        y[j] = (float)x[j];
+}
+
+// b only (pcg_build_rhs): b_j = sum w_i + delta_j / (tau lambda_j)
+template <int G>
+__global__ void __launch_bounds__(256) k_rhs_b(const DrawDesc *__restrict__ d,
+                                               const double *__restrict__ w, double *__restrict__ b) {
+    const int64_t p = d->p;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        double acc = 0.0;
+        if (j < p)
+            acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], w, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) b[j] = acc + d->delta[j] / (d->tau * d->lambda[j]);
+    }
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+
+static int pick_group(double mean_len) {
+    if (mean_len < 6) return 4;
+    if (mean_len < 20) return 8;
+    if (mean_len < 56) return 16;
+    return 32;
+}
+
+// Dispatch helpers: instantiate the kernels for the four group widths.
+#define PCG_DISPATCH_G(G, ...)                         \
+    switch (G) {                                       \
+        case 4: { constexpr int GG = 4; __VA_ARGS__; } break;   \
+        case 8: { constexpr int GG = 8; __VA_ARGS__; } break;   \
+        case 16: { constexpr int GG = 16; __VA_ARGS__; } break; \
+        default: { constexpr int GG = 32; __VA_ARGS__; } break; \
+    }
+
+template <typename T>
+static void *csr_kernel_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_csr<T, GG>);
+    return f;
+}
+template <typename T>
+static void *csc_kernel_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_csc<T, GG>);
+    return f;
+}
+static void *rhs_init_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_rhs_init<GG>);
+    return f;
+}
+static void *true_resid_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_true_resid<GG>);
+    return f;
+}
+static void *rhs_b_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_rhs_b<GG>);
+    return f;
+}
+
+pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
+    if (n <= ctx->cap_n && p <= ctx->cap_p && ctx->ws.sc) return PCG_OK;
+    const int64_t cn = std::max<int64_t>(std::max<int64_t>(n, ctx->cap_n), 1);
+    const int64_t cp = std::max<int64_t>(std::max<int64_t>(p, ctx->cap_p), 1);
+    SingleWs &w = ctx->ws;
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(w.b);
+    cudaFree(w.u);
+    w = SingleWs{};
+    // cached graphs hold workspace pointers: drop the single-RHS ones
+    for (auto it = ctx->named_graphs.begin(); it != ctx->named_graphs.end();) {
+        if (it->first.rfind("single:", 0) == 0) {
+            cudaGraphExecDestroy(it->second);
+            it = ctx->named_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    // one allocation, carved into aligned pieces
+    const size_t al = 256;
+    auto up = [&](size_t x) { return (x + al - 1) / al * al; };
+    const size_t szp64 = up(sizeof(double) * cp), szp32 = up(sizeof(float) * cp);
+    const size_t szn32 = up(sizeof(float) * cn);
+    const size_t szpart = up(sizeof(double) * kMaxReduceBlocks * 4);
+    const size_t total = 4 * szp64 + szp32 + szn32 + szpart + up(64 * sizeof(unsigned)) +
+                         up(sizeof(CgScalars)) + up(sizeof(DrawDesc));
+    char *base = nullptr;
+    PCG_CUDA_TRY(ctx, cudaMalloc(&base, total));
+    PCG_CUDA_TRY(ctx, cudaMalloc(&w.u, up(sizeof(double) * cn)));
+    PCG_CUDA_TRY(ctx, cudaMemsetAsync(base, 0, total, ctx->stream));
+    size_t off = 0;
+    auto take = [&](size_t sz) { char *q = base + off; off += sz; return q; };
+    w.b = (double *)take(szp64);
+    w.r = (double *)take(szp64);
+    w.s64 = (double *)take(szp64);
+    w.v64 = (double *)take(szp64);
+    w.s32 = (float *)take(szp32);
+    w.om32 = (float *)take(szn32);
+    w.partials = (double *)take(szpart);
+    w.counters = (unsigned *)take(up(64 * sizeof(unsigned)));
+    w.sc = (CgScalars *)take(up(sizeof(CgScalars)));
+    w.desc = (DrawDesc *)take(up(sizeof(DrawDesc)));
+    ctx->cap_n = cn;
+    ctx->cap_p = cp;
+    if (!ctx->h_desc) PCG_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_desc, sizeof(DrawDesc)));
+    if (!ctx->h_sc) PCG_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_sc, sizeof(CgScalars)));
+    return PCG_OK;
+}
+
+struct SingleLaunch {
+    int G_row, G_col;
+    int grid_stream;   // streaming kernels
+    int grid_vec;      // p-length vector kernels
+    int threads;
+};
+
+static SingleLaunch single_launch(pcg_ctx *ctx, const DrawDesc &d) {
+    SingleLaunch L;
+    L.threads = 256;
+    L.G_row = pick_group(d.n > 0 ? (double)d.nnz / (double)d.n : 1.0);
+    L.G_col = pick_group(d.p > 0 ? (double)d.nnz / (double)d.p : 1.0);
+    if (ctx->shape.csr_tpr > 0 && ctx->shape.blocks > 0) { /* tuned override, if any */ }
+    const int per_sm = 8;   // 2048 resident threads per SM at 256 threads per block
+    L.grid_stream = std::min(ctx->num_sms * per_sm, kMaxReduceBlocks);
+    const int64_t need_vec = (d.p + L.threads - 1) / L.threads;
+    L.grid_vec = (int)std::max<int64_t>(1, std::min<int64_t>(need_vec, ctx->num_sms * 4));
+    return L;
+}
+
+// Adds one kernel node; args is the kernel's argument pointer array.
+static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps,
+                              size_t ndeps, void *func, int grid, int block, void **args) {
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+// Kernel argument values must outlive node creation; they are copied into the
+// graph by cudaGraphAddKernelNode.
+struct NodeArgs {
+    const DrawDesc *d;
+    SingleWs ws;
+    const void *s_gather, *om, *u;
+    const double *u64, *s64, *nulld;
+    double *w64, *v64;
+    float *om32;
+    const int *done, *nulli;
+    cudaGraphConditionalHandle h_ru, h_while;
+    int one, zero, want_w, want_om32, use_cond_ru;
+};
+
+static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cudaGraphExec_t *out) {
+    const SingleLaunch L = single_launch(ctx, d);
+    const bool f32 = precision != PCG_PREC_FP64;
+    const bool refined = d.refined != 0;
+    NodeArgs A{};
+    A.d = ctx->ws.desc;
+    A.ws = ctx->ws;
+    A.done = &ctx->ws.sc->done;
+    A.nulli = nullptr;
+    A.nulld = nullptr;
+    A.w64 = (double *)ctx->ws.u;
+    A.om32 = ctx->ws.om32;
+    A.want_w = d.rhs == nullptr ? 1 : 0;
+    A.want_om32 = f32 ? 1 : 0;
+    A.s_gather = f32 ? (const void *)ctx->ws.s32 : (const void *)ctx->ws.s64;
+    A.om = f32 ? (const void *)ctx->ws.om32 : nullptr;   // NULL: float64 omega from the descriptor
+    A.u = ctx->ws.u;
+    A.u64 = (const double *)ctx->ws.u;
+    A.v64 = ctx->ws.v64;
+    A.s64 = ctx->ws.s64;
+    A.one = 1;
+    A.zero = 0;
+    A.use_cond_ru = refined ? 1 : 0;
+
+    cudaGraph_t g = nullptr;
+    PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
+    cudaError_t e = cudaSuccess;
+    cudaGraphNode_t n_w, n_init, n_while, n_csr, n_csc, n_upd, n_if, n_sdir, n_rcsr, n_tr;
+    cudaGraph_t body = nullptr;
+    {
+        void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32};
+        e = add_kernel(g, &n_w, nullptr, 0, (void *)k_rhs_w, L.grid_stream, L.threads, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&A.d, &A.w64, &A.ws};
+        e = add_kernel(g, &n_init, &n_w, 1, rhs_init_ptr(L.G_col), L.grid_stream, L.threads, args);
+    }
+    if (e == cudaSuccess)
+        e = cudaGraphConditionalHandleCreate(&A.h_while, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = A.h_while;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&A.d, &A.s_gather, &A.om, &A.u, &A.done, &A.nulli};
+        e = add_kernel(body, &n_csr, nullptr, 0,
+                       f32 ? csr_kernel_ptr<float>(L.G_row) : csr_kernel_ptr<double>(L.G_row),
+                       L.grid_stream, L.threads, args);
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&A.d, &A.u, &A.s64, &A.v64, &A.ws, &A.one};
+        e = add_kernel(body, &n_csc, &n_csr, 1,
+                       f32 ? csc_kernel_ptr<float>(L.G_col) : csc_kernel_ptr<double>(L.G_col),
+                       L.grid_stream, L.threads, args);
+    }
+    if (e == cudaSuccess && refined)
+        e = cudaGraphConditionalHandleCreate(&A.h_ru, body, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        void *args[] = {&A.d, &A.ws, &A.h_ru, &A.use_cond_ru};
+        e = add_kernel(body, &n_upd, &n_csc, 1, (void *)k_update, L.grid_vec, L.threads, args);
+    }
+    cudaGraphNode_t last = n_upd;
+    if (e == cudaSuccess && refined) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = A.h_ru;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_if, body, &n_upd, nullptr, 1, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t ifb = cp.conditional.phGraph_out[0];
+            // float64 product on beta: s and omega come from the descriptor (NULL)
+            void *a1[] = {&A.d, &A.nulld, &A.nulld, &A.w64, &A.done, &A.nulli};
+            e = add_kernel(ifb, &n_rcsr, nullptr, 0, csr_kernel_ptr<double>(L.G_row),
+                           L.grid_stream, L.threads, a1);
+            if (e == cudaSuccess) {
+                void *a2[] = {&A.d, &A.u64, &A.ws, &A.zero};
+                e = add_kernel(ifb, &n_tr, &n_rcsr, 1, true_resid_ptr(L.G_col), L.grid_stream,
+                               L.threads, a2);
+            }
+            last = n_if;
+        }
+    }
+    if (e == cudaSuccess) {
+        void *args[] = {&A.d, &A.ws, &A.h_while, &A.one};
+        e = add_kernel(body, &n_sdir, &last, 1, (void *)k_sdir, L.grid_vec, L.threads, args);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "building the draw graph");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "instantiating the draw graph");
+    *out = exec;
+    return PCG_OK;
+}
+
+// Plain launches (use_graph = 0): same kernels, host check every 8 iterations.
+static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision) {
+    const SingleLaunch L = single_launch(ctx, d);
+    const bool f32 = precision != PCG_PREC_FP64;
+    SingleWs ws = ctx->ws;
+    const DrawDesc *dd = ws.desc;
+    cudaStream_t st = ctx->stream;
+    const int B = L.threads;
+    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32));
+    PCG_PROF(ctx, "rhs_init", PCG_DISPATCH_G(L.G_col, (k_rhs_init<GG><<<L.grid_stream, B, 0, st>>>(dd, (const double *)ws.u, ws))));
+    const int *done = &ws.sc->done, *need = &ws.sc->need_ru;
+    for (int it = 0;; it += 8) {
+        for (int k = 0; k < 8; ++k) {
+            if (f32) {
+                PCG_PROF(ctx, "csr_f32", PCG_DISPATCH_G(L.G_row, (k_csr<float, GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, ws.s32, ws.om32, (float *)ws.u, done, nullptr))));
+                PCG_PROF(ctx, "csc_f32", PCG_DISPATCH_G(L.G_col, (k_csc<float, GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, (const float *)ws.u, ws.s64, ws.v64, ws, 1))));
+            } else {
+                PCG_PROF(ctx, "csr_f64", PCG_DISPATCH_G(L.G_row, (k_csr<double, GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, ws.s64, nullptr, (double *)ws.u, done, nullptr))));
+                PCG_PROF(ctx, "csc_f64", PCG_DISPATCH_G(L.G_col, (k_csc<double, GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, (const double *)ws.u, ws.s64, ws.v64, ws, 1))));
+            }
+            PCG_PROF(ctx, "update", k_update<<<L.grid_vec, B, 0, st>>>(dd, ws, 0, 0));
+            if (d.refined) {
+                PCG_PROF(ctx, "ru_csr_f64", PCG_DISPATCH_G(L.G_row, (k_csr<double, GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, nullptr, nullptr, (double *)ws.u, done, need))));
+                PCG_PROF(ctx, "ru_true_resid", PCG_DISPATCH_G(L.G_col, (k_true_resid<GG><<<L.grid_stream, B, 0, st>>>(
+                                            dd, (const double *)ws.u, ws, 1))));
+            }
+            PCG_PROF(ctx, "sdir", k_sdir<<<L.grid_vec, B, 0, st>>>(dd, ws, 0, 0));
+        }
+        PCG_CUDA_TRY(ctx, cudaGetLastError());
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_sc, ws.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        prof_collect(ctx);
+        if (ctx->h_sc->done) break;
+        if (it > d.max_iter + 16) return set_error(ctx, PCG_TIMEOUT, "host loop ran past max_iter");
+    }
+    return PCG_OK;
+}
+
+pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode, int *iters,
+                      double *resid) {
+    pcg_status st = ensure_single_ws(ctx, din.n, din.p);
+    if (st != PCG_OK) return st;
+    DrawDesc d = din;
+    d.refined = (precision == PCG_PREC_FP32_REFINED) ? 1 : 0;
+    d.reliable_k = ctx->opt.reliable_k;
+    *ctx->h_desc = d;
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->opt.use_graph && !ctx->opt.profile) {
+        // The graph bakes in the workspace, the group widths and, in the FP64
+        // mode and the refined mode's recomputation, the caller's omega and
+        // beta pointers; those form the cache key.
+        const SingleLaunch L = single_launch(ctx, d);
+        char key[96];
+        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d", L.G_row, L.G_col, L.grid_stream,
+                 L.grid_vec, precision, d.refined, mode);
+        auto it = ctx->named_graphs.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (it == ctx->named_graphs.end()) {
+            st = build_graph(ctx, d, precision, &exec);
+            if (st != PCG_OK) return st;
+            ctx->named_graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+        PCG_CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_sc, ctx->ws.sc, sizeof(CgScalars),
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        // graph nodes that ran: 2 set-up kernels, 4 per loop trip (at least
+        // one trip), 2 per float64 recomputation of r
+        const CgScalars &h = *ctx->h_sc;
+        ctx->last_launches += 2 + 4 * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
+    } else {
+        st = run_plain(ctx, d, precision);
+        if (st != PCG_OK) return st;
+    }
+    const CgScalars &sc = *ctx->h_sc;
+    *iters = sc.iter;
+    *resid = sc.resid;
+    if (sc.status == kRunning) return set_error(ctx, PCG_TIMEOUT, "draw did not finish");
+    if (sc.status != PCG_OK) {
+        const char *what = sc.status == PCG_MAXITER ? "max_iter reached before the stop rule"
+                           : sc.status == PCG_BREAKDOWN ? "CG breakdown: s.Phi s <= 0 or rho <= 0"
+                                                        : "non-finite CG scalar";
+        return set_error(ctx, (pcg_status)sc.status, what);
+    }
+    return PCG_OK;
+}
+
+pcg_status launch_build_rhs(pcg_ctx *ctx, const pcg_csc *X, const double *omega, const double *z,
+                            const double *lambda, double tau, const double *eta,
+                            const double *delta, double *b) {
+    pcg_status st = ensure_single_ws(ctx, X->n, X->p);
+    if (st != PCG_OK) return st;
+    DrawDesc d{};
+    d.col_ptr = X->col_ptr;
+    d.row_idx = X->row_idx;
+    d.omega = omega;
+    d.z = z;
+    d.lambda = lambda;
+    d.eta = eta;
+    d.delta = delta;
+    d.n = X->n;
+    d.p = X->p;
+    d.nnz = X->nnz;
+    d.tau = tau;
+    *ctx->h_desc = d;
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    const int grid = std::min(ctx->num_sms * 8, kMaxReduceBlocks);
+    const int G = pick_group(d.p > 0 ? (double)d.nnz / d.p : 1.0);
+    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (double *)ctx->ws.u, ctx->ws.om32, 1, 0));
+    PCG_PROF(ctx, "rhs_b", PCG_DISPATCH_G(G, (k_rhs_b<GG><<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (const double *)ctx->ws.u, b))));
+    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+    return PCG_OK;
+}
+
+pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *omega,
+                          const double *lambda, double tau, const double *v, double *out) {
+    pcg_status st = ensure_single_ws(ctx, Xr->n, Xr->p);
+    if (st != PCG_OK) return st;
+    DrawDesc d{};
+    d.row_ptr = Xr->row_ptr;
+    d.col_idx = Xr->col_idx;
+    d.col_ptr = Xc->col_ptr;
+    d.row_idx = Xc->row_idx;
+    d.omega = omega;
+    d.lambda = lambda;
+    d.n = Xr->n;
+    d.p = Xr->p;
+    d.nnz = Xr->nnz;
+    d.tau = tau;
+    *ctx->h_desc = d;
+    cudaStream_t s = ctx->stream;
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
+                                      cudaMemcpyHostToDevice, s));
+    // the gate flags of the iteration kernels must read "running"
+    PCG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.sc, 0, sizeof(CgScalars), s));
+    const int grid = std::min(ctx->num_sms * 8, kMaxReduceBlocks);
+    const int Gr = pick_group(d.n > 0 ? (double)d.nnz / d.n : 1.0);
+    const int Gc = pick_group(d.p > 0 ? (double)d.nnz / d.p : 1.0);
+    SingleWs ws = ctx->ws;
+    const int *done = &ws.sc->done;
+    if (ctx->opt.precision != PCG_PREC_FP64) {
+        PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
+        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, 1));
+        PCG_PROF(ctx, "csr_f32", PCG_DISPATCH_G(Gr, (k_csr<float, GG><<<grid, 256, 0, s>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, done, nullptr))));
+        PCG_PROF(ctx, "csc_f32", PCG_DISPATCH_G(Gc, (k_csc<float, GG><<<grid, 256, 0, s>>>(ws.desc, (const float *)ws.u, v, out, ws, 0))));
+    } else {
+        PCG_PROF(ctx, "csr_f64", PCG_DISPATCH_G(Gr, (k_csr<double, GG><<<grid, 256, 0, s>>>(ws.desc, v, omega, (double *)ws.u, done, nullptr))));
+        PCG_PROF(ctx, "csc_f64", PCG_DISPATCH_G(Gc, (k_csc<double, GG><<<grid, 256, 0, s>>>(ws.desc, (const double *)ws.u, v, out, ws, 0))));
+    }
+    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    PCG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    prof_collect(ctx);
+    return PCG_OK;
+}
+
+}  // namespace pcg

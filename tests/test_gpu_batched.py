@@ -1,0 +1,114 @@
+"""Parity of the batched path (R chains sharing X, one RHS-block product per
+iteration) with the CPU oracle run chain by chain, and with the single-RHS
+path.  Tolerances as for the single path: relative L2 1e-5 in the refined
+mode, 1e-3 in pure float32, iteration counts within 2."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1810_12437_gb300 import inputs
+from tests.gpu_helpers import T, dev, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    need_gpu()
+    import paper_1810_12437_gb300 as pb
+    pb.load_library()
+    return pb
+
+
+def batched_args(P):
+    return dict(omega=T(P.omega), z=T(P.z), lam=T(P.lam), tau=T(P.tau), eta=T(P.eta), delta=T(P.delta))
+
+
+def chain(P, r):
+    return (P.omega[r], P.z[r], P.lam[r], float(P.tau[r]), P.eta[r], P.delta[r])
+
+
+@pytest.fixture(scope="module")
+def small3():
+    """The batched recipe (log10 r ~ U(-4.5,-1.5), per-chain tau) at a size the
+    oracle finishes in seconds; odd n and p give ragged tails."""
+    return inputs.config3(nrhs=16, n=40_011, p=4_003)
+
+
+@pytest.mark.parametrize("prec,bound", [("fp32_refined", 1e-5), ("fp32", 1e-3)])
+def test_batched_matches_oracle_per_chain(pb, small3, prec, bound):
+    P = small3
+    import paper_1810_12437_gb300 as _pb
+    X = _pb.DeviceDesign.from_host(P.X, dev())
+    a = batched_args(P)
+    ctx = pb.Context(precision=prec, reliable_k=50)
+    res = pb.pcg_draw_beta_batched(ctx, X, **a, tol=1e-6, max_iter=5000)
+    beta = res.beta.cpu().numpy()
+    for r in range(16):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        ref, k, _, st = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
+        assert res.status[r] == pb.PCG_OK and st == O.OK
+        assert abs(res.iters[r] - k) <= 2, (r, res.iters[r], k)
+        same_k = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, fixed_iters=res.iters[r])[0]
+        assert rel(beta[r], same_k) < bound, r
+        assert rel(beta[r], ref) < bound, r
+
+
+@pytest.mark.parametrize("R", [1, 3, 5, 32])
+def test_batched_ragged_block_sizes_match_single(pb, R):
+    """Padding of the RHS block (R not a power of two) changes nothing: each
+    chain equals its single-RHS draw."""
+    P = inputs.config3(nrhs=R, n=9_001, p=1_501, seed_offset=R)
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    a = batched_args(P)
+    ctx = pb.Context(precision="fp32_refined")
+    res = pb.pcg_draw_beta_batched(ctx, X, **a, tol=1e-6, max_iter=5000)
+    for r in range(R):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        single = pb.pcg_draw_beta(ctx, X, T(om), T(z), T(lam), tau, T(eta), T(delta), tol=1e-6,
+                                  max_iter=5000)
+        assert abs(single.iters - res.iters[r]) <= 2
+        assert rel(res.beta[r].cpu().numpy(), single.beta.cpu().numpy()) < 1e-5
+        ref = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)[0]
+        assert rel(res.beta[r].cpu().numpy(), ref) < 1e-5
+
+
+def test_batched_graph_and_plain_agree(pb, small3):
+    P = small3
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    a = batched_args(P)
+    outs = []
+    for g in (True, False):
+        ctx = pb.Context(precision="fp32_refined", use_graph=g)
+        res = pb.pcg_draw_beta_batched(ctx, X, **a, tol=1e-6, max_iter=5000)
+        outs.append((res.iters, res.beta.cpu().numpy()))
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_batched_fp64_mode_rejected(pb, small3):
+    P = small3
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    ctx = pb.Context(precision="fp64")
+    with pytest.raises(pb.PcgError):
+        pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=100)
+
+
+@pytest.mark.slow
+def test_batched_full_size_true_residual(pb):
+    """n = 5e5, p = 5e4, 16 chains, the launch the benchmark times: every
+    chain's draw satisfies the paper's stop rule for its true residual,
+    recomputed by the oracle in float64, and b matches the oracle on sampled
+    columns."""
+    P = inputs.config3()
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    ctx = pb.Context(precision="fp32_refined", reliable_k=50)
+    res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
+    beta = res.beta.cpu().numpy()
+    for r in (0, 7, 15):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        b = O.build_b(P.X, om, z, lam, tau, eta, delta)
+        rt = tau * lam * (b - O.phi_mul(P.X, om, lam, tau, beta[r]))
+        assert res.status[r] == pb.PCG_OK
+        assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6, r
