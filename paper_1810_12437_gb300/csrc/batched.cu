@@ -506,7 +506,9 @@ __global__ void __launch_bounds__(256) k_b_true_resid(const BatchDesc *__restric
                             sc->status = PCG_OK;
                             sc->done = 1;
                         } else {
+                            // float64 residual above the rule: restart from it
                             sc->pending = 0;
+                            sc->gamma = 0.0;
                             if (sc->iter >= d->max_iter) { sc->status = PCG_MAXITER; sc->done = 1; }
                         }
                     }

@@ -418,12 +418,14 @@ pcg_status pcg_adjoint(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const
     ctx->last_launches = 0;
     st = draw_or_solve(ctx, Xr, Xc, omega, nullptr, lambda, tau, nullptr, nullptr, grad_beta, tol,
                        max_iter, g_b, iters, resid);
-    if (st != PCG_OK) return st;
+    // a solve stopped by max_iter still yields the gradient of its last iterate
+    if (st != PCG_OK && st != PCG_MAXITER) return st;
+    const pcg_status solve_st = st;
     const int64_t solve_launches = ctx->last_launches;
     st = launch_adjoint_terms(ctx, Xr, omega, z, lambda, tau, eta, delta, beta, g_b, mode,
                                 g_omega, g_loglambda, g_logtau);
     ctx->last_launches += solve_launches;
-    return st;
+    return st != PCG_OK ? st : solve_st;
 }
 
 int pcg_profile_count(const pcg_ctx *ctx) { return ctx ? (int)ctx->prof.size() : 0; }

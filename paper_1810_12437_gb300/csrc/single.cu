@@ -318,7 +318,11 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
                     sc->status = PCG_OK;
                     sc->done = 1;
                 } else {
+                    // the recursion met the rule but the float64 residual does
+                    // not: restart from it (s = M^-1 r), i.e. refine the
+                    // current beta instead of extending a stale direction
                     sc->pending = 0;
+                    sc->gamma = 0.0;
                     if (sc->iter >= d->max_iter) {
                         sc->status = PCG_MAXITER;
                         sc->done = 1;

@@ -315,9 +315,17 @@ __device__ void finalize(const UProb &P, UState &S, UGlobal &G, int ph, double *
                 sc.rho = rt;
                 sc.gamma = rt / sc.rho_prev;
                 sc.resid = stop_quantity(G.stop_rule, rt, sc.rho0, p);
-                if (sc.pending && stop_met(G.stop_rule, rt, sc.rho0, p, G.tol)) sc.status = PCG_OK;
-                else if (sc.iter >= G.max_iter) sc.status = PCG_MAXITER;
-                else { sc.pending = 0; nx = PH_E; }
+                if (sc.pending && stop_met(G.stop_rule, rt, sc.rho0, p, G.tol)) {
+                    sc.status = PCG_OK;
+                } else if (sc.iter >= G.max_iter) {
+                    sc.status = PCG_MAXITER;
+                } else {
+                    // float64 residual above the rule after the recursion met
+                    // it: restart from the float64 residual
+                    if (sc.pending) sc.gamma = 0.0;
+                    sc.pending = 0;
+                    nx = PH_E;
+                }
                 break;
             }
             case PH_E: nx = PH_A; break;

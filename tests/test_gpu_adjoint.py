@@ -21,15 +21,16 @@ def pb():
 
 
 @pytest.mark.parametrize("mode", ["draw", "solve"])
-@pytest.mark.parametrize("prec,bound", [("fp64", 1e-8), ("fp32_refined", 1e-5)])
-def test_adjoint_matches_cholesky_gradient(pb, mode, prec, bound):
+@pytest.mark.parametrize("prec,bound,tol", [("fp64", 1e-8, 1e-12), ("fp32_refined", 1e-5, 1e-9)])
+def test_adjoint_matches_cholesky_gradient(pb, mode, prec, bound, tol):
     P = inputs.config5_small()
     X, a = device_problem(P)
     ctx = pb.Context(precision=prec, stop_rule="relative")
     dr = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"],
-                          tol=1e-12, max_iter=5000)
+                          tol=tol, max_iter=5000)
     g = pb.pcg_adjoint(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta,
-                       T(P.c), mode=mode, tol=1e-12, max_iter=5000)
+                       T(P.c), mode=mode, tol=tol, max_iter=5000)
+    assert dr.status == pb.PCG_OK and g["status"] == pb.PCG_OK
     beta_c, gc = O.adjoint_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, P.c, mode=mode)
     assert rel(dr.beta.cpu().numpy(), beta_c) < bound
     for key in ("b", "omega", "log_lambda"):
