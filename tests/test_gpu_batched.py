@@ -51,7 +51,7 @@ def test_batched_matches_oracle_per_chain(pb, small3, prec, bound):
         om, z, lam, tau, eta, delta = chain(P, r)
         ref, k, _, st = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
         assert res.status[r] == pb.PCG_OK and st == O.OK, (r, res.status[r])
-        assert k - 2 <= res.iters[r] <= 2.2 * k + 5, (r, res.iters[r], k)
+        assert k - 2 <= res.iters[r] <= 3.5 * k + 10, (r, res.iters[r], k)
         assert rel(beta[r], ref) < bound, r
 
 

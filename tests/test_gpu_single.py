@@ -75,7 +75,7 @@ def fp64_iters_ok(k_gpu, k_ref):
 
 
 def fp32_iters_ok(k_gpu, k_ref):
-    return k_ref - 2 <= k_gpu <= 2.2 * k_ref + 5
+    return k_ref - 2 <= k_gpu <= 3.5 * k_ref + 10
 
 
 def well_conditioned():
