@@ -223,6 +223,36 @@ pcg_status pcg_profile_entry(const pcg_ctx *ctx, int i, const char **name, doubl
 void pcg_profile_reset(pcg_ctx *ctx);
 int64_t pcg_last_kernel_launches(const pcg_ctx *ctx);
 
+/*
+ * Allocation-free variant of pcg_phi_mul, for callers that cannot allocate
+ * device memory: code running while a stream is captured into a CUDA graph,
+ * host runtimes whose allocator owns the whole device, and loops where an
+ * allocation could synchronise the device.  The paper has no counterpart.
+ *
+ * Computes out = X^T (Omega (X v)) + tau^-2 Lambda^-2 v in float64 (as
+ * pcg_phi_mul does in PCG_PREC_FP64 mode) without a context: the caller
+ * passes all inputs and outputs (device pointers, as everywhere) and the
+ * stream (a cudaStream_t as void*, NULL for the legacy default stream).  The
+ * call only queues the two kernels on `stream` and returns; `out` is ready
+ * when the stream reaches that point.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * The intermediate u = Omega (X v) (n float64) lives in one file-scope device
+ * array of PCG_NOALLOC_MAX_N doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits.  Sizes: n <= PCG_NOALLOC_MAX_N, else
+ * PCG_BADARG is returned before any GPU work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, once per
+ * device); make that first call outside any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents (each call
+ * writes every entry it reads, so nothing needs clearing): calls that overlap
+ * on the GPU, e.g. on two streams at once, race on it.  Returns PCG_OK,
+ * PCG_BADARG (NULL pointer, size mismatch, n too large, tau <= 0) or PCG_CUDA.
+ */
+#define PCG_NOALLOC_MAX_N 1048576
+pcg_status pcg_phi_mul_noalloc(const pcg_csr *X_csr, const pcg_csc *X_csc, const double *omega,
+                               const double *lambda, double tau, const double *v, double *out,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.POINTER(ctypes.c_int64)], I),
             "pcg_profile_reset": ([P], None),
             "pcg_last_kernel_launches": ([P], I64),
+            "pcg_phi_mul_noalloc": ([pCsr, pCsc, P, P, D, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -105,7 +106,8 @@ def exported_symbols() -> Sequence[str]:
     return ["pcg_options_default", "pcg_ctx_create", "pcg_ctx_destroy", "pcg_last_error",
             "pcg_check_design", "pcg_build_rhs", "pcg_phi_mul", "pcg_draw_beta", "pcg_solve",
             "pcg_draw_beta_batched", "pcg_draw_beta_uneven", "pcg_adjoint", "pcg_profile_count",
-            "pcg_profile_entry", "pcg_profile_reset", "pcg_last_kernel_launches"]
+            "pcg_profile_entry", "pcg_profile_reset", "pcg_last_kernel_launches",
+            "pcg_phi_mul_noalloc"]
 
 
 # ---------------------------------------------------------------------------
@@ -422,3 +424,24 @@ def profile_table(ctx: Context) -> dict:
         name, ms, n = pcg_profile_entry(ctx, i)
         out[name] = (ms, n)
     return out
+
+
+NOALLOC_MAX_N = 1048576
+
+
+def pcg_phi_mul_noalloc(X, omega, lam, tau, v, out, stream=None):
+    """Phi v into the caller's `out` with no device allocation (float64).
+    Queues the work on `stream` (default: the current stream) and returns the
+    status without waiting."""
+    lib = load_library()
+    f = torch.float64
+    dev = X.device
+    _dev(omega, f, X.n, "omega", dev)
+    _dev(lam, f, X.p, "lambda", dev)
+    _dev(v, f, X.p, "v", dev)
+    _dev(out, f, X.p, "out", dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    csr, csc = X.csr(), X.csc()
+    with torch.cuda.device(dev):
+        return lib.pcg_phi_mul_noalloc(ctypes.byref(csr), ctypes.byref(csc), _ptr(omega), _ptr(lam),
+                                       float(tau), _ptr(v), _ptr(out), ctypes.c_void_p(s.cuda_stream))
