@@ -39,6 +39,8 @@ METRIC = "beta-draws/sec and SpMV HBM GB/s vs peak at n=5e5,p=5e4; batched/adjoi
 UNIT = "beta-draws/s"
 NRHS = 16
 TOL = 1e-6
+PRECISION = os.environ.get("PCG_BENCH_PRECISION", "fp32_refined")
+RELIABLE_K = 50
 WORKLOAD = ("16 chains sharing binary X, n=500000, p=50000, log10 r_j~U(-4.5,-1.5), "
             "per-chain omega~U(.05,.25), half-Cauchy lambda (2% x100), log10 tau~U(-3.5,-2.5), "
             "paper RMS stop 1e-6")
@@ -54,6 +56,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the single-RHS comparator, e2e and CPU baseline legs")
     ap.add_argument("--small", action="store_true", help="debug: a 20x smaller design")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the uneven-batch and adjoint comparisons")
     return ap.parse_args()
 
 
@@ -128,6 +132,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, device=None):
+    """Max of a per-rank time over all ranks (the job's step time)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ms_per_step):
+    """Whole-job draws/s: every rank draws NRHS chains per step."""
+    return world * NRHS / (ms_per_step / 1e3)
+
+
 def make_workload(rank, small):
     from paper_1810_12437_gb300 import inputs
     if small:
@@ -135,10 +155,30 @@ def make_workload(rank, small):
     return inputs.config3(nrhs=NRHS, seed_offset=rank)
 
 
-def bytes_per_launch(kernel, n, p, nnz, RP):
-    """Algorithmic bytes of one launch of the batched kernels: every index read
-    once, every gathered vector read once (it is L2-resident), every output
-    written once."""
+def tile_geometry(n, p, RG, vsize=4):
+    """Tile widths of the shared-memory tiled products (the library's rule:
+    220 KB of staged values including one zero sentinel slot, at most 65528
+    per 16-bit offset, a multiple of 8)."""
+    w = min((220 * 1024 - RG * vsize) // (RG * vsize), 65528) & ~7
+    wc, wr = min(w, p), min(w, n)
+    return (p + wc - 1) // wc, (n + wr - 1) // wr
+
+
+def bytes_per_launch(kernel, n, p, nnz, RP, RG=1):
+    """Algorithmic bytes of one launch: every stored index read once (2 bytes,
+    pad slots not counted), chunk bounds, every gathered vector read once (it
+    is staged on chip), every output written once.  Values are 4 bytes in the
+    float32 kernels and 8 bytes in the double-float ones (pairs of floats
+    staged, float64 partial sums)."""
+    vs = 8 if kernel.endswith("df32") else 4
+    if kernel in ("bt_csr_f32", "t_csr_f32", "bt_csr_df32", "t_csr_df32"):
+        Tc, _ = tile_geometry(n, p, RG, vs)
+        return 2 * nnz + 4 * (Tc * n + 1) + vs * RG * p + vs * RG * Tc * n
+    if kernel in ("bt_csc_f32", "t_csc_f32", "bt_csc_df32", "t_csc_df32"):
+        Tc, Tr = tile_geometry(n, p, RG, vs)
+        return 2 * nnz + 4 * (Tr * p + 1) + 4 * p + vs * RG * (Tc * n + n) + vs * RG * Tr * p
+    if kernel == "bt_fin":
+        return None
     if kernel == "b_csr_f32":
         return 4 * nnz + 8 * (n + 1) + 4 * n * RP + 4 * n * RP + 4 * p * RP
     if kernel == "b_csc_f32":
@@ -147,16 +187,16 @@ def bytes_per_launch(kernel, n, p, nnz, RP):
         return 4 * nnz + 8 * (n + 1) + 8 * n * RP + 8 * n * RP + 8 * p * RP
     if kernel == "b_ru_true_resid":
         return 4 * nnz + 8 * (p + 1) + 8 * n * RP + 5 * 8 * p * RP
-    if kernel in ("b_update",):
+    if kernel == "b_update":
         return 6 * 8 * p * RP
-    if kernel in ("b_sdir",):
+    if kernel == "b_sdir":
         return 3 * 8 * p * RP + 4 * p * RP
     return None
 
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("batched.cu", "device_common.cuh", "internal.h"):
+    for f in ("batched.cu", "tiled.cu", "tiled.h", "device_common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_1810_12437_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -197,7 +237,11 @@ def run_ours(args):
     ins = dict(omega=T(P.omega), z=T(P.z), lam=T(P.lam), tau=T(P.tau), eta=T(P.eta), delta=T(P.delta))
     out = torch.empty((NRHS, P.X.p), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream)
+    # the autotuned launch shapes are shared (through the cache file) with the
+    # profiled pass below, so that the roofline describes the timed layout
+    import tempfile
+    tune_file = os.path.join(tempfile.mkdtemp(prefix="pcg_tune_"), "autotune.txt")
+    ctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, autotune_cache=tune_file)
 
     def step():
         return pb.pcg_draw_beta_batched(ctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
@@ -225,18 +269,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * NRHS / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = job_value(world, ms)
     statuses = list(res.status)
 
     extras = {}
     if not args.no_extras:
         # plain single-RHS PCG on the same GPU and accuracy: the 16 chains one by one
-        sctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream)
+        sctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream)
         s_iters = []
         ch = lambda a, r: a[r].contiguous()
         for r in range(NRHS):   # warm-up and graph capture on chain 0 first
@@ -281,35 +321,45 @@ def run_ours(args):
             e2e_step()
         ee1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = ee0.elapsed_time(ee1) / ne
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        extras["e2e"] = {"value": world * NRHS / (e2e_ms / 1e3), "unit": UNIT,
+        e2e_ms = max_over_ranks(ee0.elapsed_time(ee1) / ne, world, dev)
+        extras["e2e"] = {"value": job_value(world, e2e_ms), "unit": UNIT,
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                          "note": "X resident (fixed design); per-step chain inputs host->device"}
 
     # roofline of the dominant kernel: per-kernel CUDA events on the launching stream
-    pctx = pb.Context(precision="fp32_refined", reliable_k=50, stream=stream, profile=True)
+    pctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, profile=True,
+                      autotune_cache=tune_file)
     pb.pcg_draw_beta_batched(pctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
     table = pb.profile_table(pctx)
     RP = 16
+    # group width the autotuner chose: RP / RG tiled CSR launches per update launch
+    RG = 1
+    tiled_csr = "bt_csr_df32" if "bt_csr_df32" in table else "bt_csr_f32"
+    if tiled_csr in table and "b_update" in table:
+        # launches of one group's products per update launch (before compaction)
+        RG = max(1, round(RP * table["b_update"][1] / max(table[tiled_csr][1], 1)))
     top = max(table.items(), key=lambda kv: kv[1][0])
     kname, (kms, kn) = top
     avg_s = kms / kn / 1e3
-    bpl = bytes_per_launch(kname, P.X.n, P.X.p, P.X.nnz, RP)
+    bpl = bytes_per_launch(kname, P.X.n, P.X.p, P.X.nnz, RP, RG)
     peak, peak_kind = peaks()
     achieved = bpl / avg_s / 1e9 if bpl else None
     total_ms = sum(v[0] for v in table.values())
+    per_k = {}
+    for k, v in sorted(table.items()):
+        bb = bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP, RG)
+        per_k[k] = {"avg_us": round(v[0] / v[1] * 1e3, 2), "launches": v[1],
+                    "GBps": round(bb / (v[0] / v[1] / 1e3) / 1e9, 1) if bb else None}
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic_for(kname),
             "peak_source": f"hbm_gbs of {peak_kind}", "avg_launch_us": avg_s * 1e6,
-            "algorithmic_bytes_per_launch": bpl,
+            "algorithmic_bytes_per_launch": bpl, "rhs_group": RG,
             "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in sorted(table.items())},
-            "per_kernel_GBps": {k: (bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP) / (v[0] / v[1] / 1e3) / 1e9
-                                    if bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP) else None)
-                                for k, v in sorted(table.items())}}
+            "per_kernel": per_k}
+
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = other_forms(pb, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -320,18 +370,79 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": P.X.n, "p": P.X.p, "nnz": P.X.nnz, "nrhs": NRHS,
-                   "tol": TOL, "precision": "fp32 products, fp64 scalars, fp64 reliable update every 50",
+                   "tol": TOL, "precision": PRECISION,
                    "parallelism": f"replicas x{world} (independent chains per GPU)",
                    "l2": "inputs larger than L2 (0.92 GB of index streams per iteration)",
                    "iters_per_chain": iters[-1], "status": statuses},
         "e2e": extras.get("e2e"), "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
-        "single_rhs": extras.get("single_rhs"), "clocks": clk,
+        "single_rhs": extras.get("single_rhs"), "clocks": clk, "forms": forms,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def other_forms(pb, dev, stream):
+    """The uneven batch and the adjoint, each against plain single-RHS PCG on
+    the same GPU, same precision (fp32 refined) and stop rule (RMS 1e-6)."""
+    import torch
+    from paper_1810_12437_gb300 import inputs
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    out = {}
+    # uneven batch: 64 problems, n ~ logU[5e3, 2e5], p ~ logU[1e3, 3e4]
+    probs = inputs.config4()
+    dp = [dict(X=pb.DeviceDesign.from_host(P.X, dev), omega=T(P.omega), z=T(P.z), lam=T(P.lam),
+               tau=float(P.tau), eta=T(P.eta), delta=T(P.delta)) for P in probs]
+    ctx = pb.Context(precision="fp32_refined", stream=stream)
+    pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)          # tunes and builds the graph
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    res = pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)
+    torch.cuda.synchronize(dev)
+    t_uneven = time.perf_counter() - t0
+    sctx = pb.Context(precision="fp32_refined", stream=stream)
+    for d in dp[:2]:
+        pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"], tol=TOL)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s_iters = []
+    for d in dp:
+        r = pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"],
+                             tol=TOL, max_iter=20_000)
+        s_iters.append(r.iters)
+    torch.cuda.synchronize(dev)
+    t_single = time.perf_counter() - t0
+    out["uneven"] = {"workload": "64 problems, n~logU[5e3,2e5], p~logU[1e3,3e4], log10 r~U(-4,-1.5), tau=0.01",
+                     "nnz_total": int(sum(P.X.nnz for P in probs)),
+                     "persistent_kernel_draws_per_s": len(dp) / t_uneven,
+                     "single_rhs_draws_per_s": len(dp) / t_single,
+                     "iters_sum_uneven": int(sum(r.iters for r in res)), "iters_sum_single": int(sum(s_iters)),
+                     "status_ok": all(r.status == 0 for r in res)}
+    del dp
+    # adjoint: gradient of c^T beta on n=2e5, p=2e4
+    P = inputs.config5()
+    X = pb.DeviceDesign.from_host(P.X, dev)
+    a = dict(omega=T(P.omega), z=T(P.z), lam=T(P.lam), eta=T(P.eta), delta=T(P.delta))
+    actx = pb.Context(precision="fp32_refined", stream=stream)
+    dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
+    pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta, T(P.c), tol=TOL)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
+    torch.cuda.synchronize(dev)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta, T(P.c),
+                       tol=TOL)
+    torch.cuda.synchronize(dev)
+    t_adj = time.perf_counter() - t0
+    out["adjoint"] = {"workload": "n=200000, p=20000, log10 r~U(-4,-1.8), tau=1e-3, L = c^T beta",
+                      "forward_draws_per_s": 1.0 / t_fwd, "adjoint_gradients_per_s": 1.0 / t_adj,
+                      "forward_iters": dr.iters, "adjoint_iters": g["iters"],
+                      "adjoint_over_forward_time": t_adj / t_fwd}
+    return out
 
 
 def cpu_baseline(P, gpu_iters):

@@ -65,7 +65,11 @@ enum {
     PCG_PREC_FP32_REFINED = 1,  /* float32 gathers and sums; CG scalars, beta and r in
                                    float64; r = b - Phi beta recomputed in float64
                                    every reliable_k iterations and before stopping */
-    PCG_PREC_FP32 = 2           /* float32 products, float64 scalars, no recomputation */
+    PCG_PREC_FP32 = 2,          /* float32 products, float64 scalars, no recomputation */
+    PCG_PREC_DF32 = 3           /* double-float products: each gathered value held as a pair
+                                   of float32 (hi + lo) and summed with error-free float32
+                                   TwoSum, about 48 significant bits at float32 arithmetic
+                                   cost; CG scalars, beta and r in float64 */
 };
 
 /* Stop rules.  With rho = r.(M^-1 r) = ||tau lambda (.) r||^2 (Sec. S4.2):

@@ -11,11 +11,14 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "tiled.h"
 
 namespace pcg {
 
@@ -30,7 +33,16 @@ struct BatchDesc {
     int R, RP;
     double tol;
     int max_iter, stop_rule, refined, reliable_k;
+    int RG;   // right-hand sides per tiled product group (0: untiled products)
 };
+
+// flags[] layout (kFlagInts ints, device):
+//   [0] all chains done, [1] some chain needs the float64 recomputation,
+//   [2] iterations that ran it, [3] a compaction was planned this iteration,
+//   [4] active product groups, [5] compactions so far,
+//   [32 + s] chain held by slot s, [64 + s] old slot moved to slot s by the compaction,
+//   [96 + g] 1 when product group g holds no live chain (its products are skipped).
+constexpr int kFlagInts = 128;
 
 struct BatchWs {
     double *b, *r, *s64, *v64, *beta, *m, *dg;   // p*RP each (interleaved)
@@ -41,7 +53,7 @@ struct BatchWs {
     double *partials;                            // kMaxReduceBlocks * 32
     unsigned int *counters;                      // 16
     CgScalars *sc;                               // 32
-    int *flags;                                  // [0] all done, [1] any needs the recomputation
+    int *flags;                                  // see the layout above
     BatchDesc *desc;
 };
 
@@ -243,6 +255,14 @@ __global__ void __launch_bounds__(256) k_b_init(const BatchDesc *__restrict__ d,
             ws.flags[0] = all;
             ws.flags[1] = 0;
             ws.flags[2] = 0;
+            ws.flags[3] = 0;
+            ws.flags[4] = d->RG > 0 ? RP / d->RG : 1;
+            ws.flags[5] = 0;
+        }
+        if (threadIdx.x < 32) {
+            ws.flags[96 + threadIdx.x] = 0;
+            ws.flags[32 + threadIdx.x] = threadIdx.x;
+            ws.flags[64 + threadIdx.x] = threadIdx.x;
         }
     }
 }
@@ -348,6 +368,59 @@ __global__ void __launch_bounds__(256) k_b_csc(const BatchDesc *__restrict__ d,
                 else if (!(sigma > 0.0) || !(sc->rho > 0.0)) { sc->status = PCG_BREAKDOWN; sc->done = 1; }
                 else sc->alpha = sc->rho / sigma;
             }
+        }
+    }
+}
+
+// Tiled products: v = sum_t Pc[t] + d s (float64), sigma per chain, alpha.
+template <int RP, typename PT>
+__global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
+                                               const PT *__restrict__ Pc, int T_r, BatchWs ws) {
+    __shared__ double part[8][RP];
+    __shared__ double vals[RP];
+    __shared__ double sums[RP];
+    if (*(volatile const int *)&ws.flags[0]) return;
+    const int64_t p = d->p;
+    const int R = d->R;
+    const int r = threadIdx.x % RP;          // fixed per thread: the stride is a multiple of RP
+    double sg = 0.0;
+    const int64_t total = p * RP;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        PT acc = Pc[t];
+        for (int k = 1; k < T_r; ++k) acc += Pc[(size_t)k * total + t];
+        const double s = ws.s64[t];
+        const double v = (double)acc + ws.dg[t] * s;
+        ws.v64[t] = v;
+        sg += s * v;
+    }
+#pragma unroll
+    for (int o = 16; o >= RP; o >>= 1) sg += __shfl_xor_sync(kFull, sg, o);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane < RP) part[wib][lane] = sg;
+    __syncthreads();
+    if (threadIdx.x < RP) {
+        double a = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += part[w2][threadIdx.x];
+        vals[threadIdx.x] = a;
+    }
+    if (grid_reduce_arr<RP>(vals, ws.partials, ws.counters + 1, sums)) {
+        const int q = threadIdx.x;
+        if (q < R) {
+            CgScalars *sc = ws.sc + q;
+            if (!sc->done) {
+                const double sigma = sums[q];
+                sc->sigma = sigma;
+                if (!isfinite(sigma)) { sc->status = PCG_NONFINITE; sc->done = 1; }
+                else if (!(sigma > 0.0) || !(sc->rho > 0.0)) { sc->status = PCG_BREAKDOWN; sc->done = 1; }
+                else sc->alpha = sc->rho / sigma;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int k = 0; k < R; ++k) all &= ws.sc[k].done ? 1 : 0;
+            ws.flags[0] = all;
         }
     }
 }
@@ -544,16 +617,97 @@ __global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d,
     }
 }
 
+// Compaction (tiled products only): when the live chains fit in fewer product
+// groups than are active, move them to the lowest slots (finished chains keep
+// their state in the slots after them) and switch the freed groups off.  One
+// block decides; k_b_compact_apply then permutes every per-chain row.
+template <int RP>
+__global__ void k_b_compact_plan(const BatchDesc *__restrict__ d, BatchWs ws) {
+    __shared__ CgScalars tmp[RP];
+    __shared__ int perm[RP], chain[RP], go;
+    const int R = d->R, RG = d->RG;
+    if (threadIdx.x == 0) {
+        go = 0;
+        if (RG > 0 && !ws.flags[0]) {
+            int live = 0;
+            for (int s = 0; s < R; ++s) live += ws.sc[s].done ? 0 : 1;
+            const int need = (live + RG - 1) / RG;
+            if (need < ws.flags[4]) {
+                int k = 0;
+                for (int s = 0; s < R; ++s)
+                    if (!ws.sc[s].done) perm[k++] = s;
+                for (int s = 0; s < R; ++s)
+                    if (ws.sc[s].done) perm[k++] = s;
+                for (int s = R; s < RP; ++s) perm[s] = s;
+                go = 1;
+                ws.flags[4] = need;
+                ws.flags[5] += 1;
+            }
+        }
+        ws.flags[3] = go;
+    }
+    __syncthreads();
+    if (!go) return;
+    const int s = threadIdx.x;
+    if (s < RP) {
+        tmp[s] = ws.sc[perm[s]];
+        chain[s] = ws.flags[32 + perm[s]];
+    }
+    __syncthreads();
+    if (s < RP) {
+        ws.sc[s] = tmp[s];
+        ws.flags[32 + s] = chain[s];
+        ws.flags[64 + s] = perm[s];
+    }
+    if (s < 32) ws.flags[96 + s] = (s >= ws.flags[4]) ? 1 : 0;
+}
+
+template <int RP, typename V>
+__device__ __forceinline__ void permute_row(V *row, const int *perm) {
+    V v[RP];
+#pragma unroll
+    for (int s = 0; s < RP; ++s) v[s] = row[s];
+#pragma unroll
+    for (int s = 0; s < RP; ++s) row[s] = v[perm[s]];
+}
+
+template <int RP>
+__global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__restrict__ d, BatchWs ws) {
+    __shared__ int perm[RP];
+    if (!*(volatile const int *)&ws.flags[3]) return;
+    if (threadIdx.x < RP) perm[threadIdx.x] = ws.flags[64 + threadIdx.x];
+    __syncthreads();
+    const int64_t p = d->p, n = d->n;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const size_t o = (size_t)j * RP;
+        permute_row<RP>(ws.b + o, perm);
+        permute_row<RP>(ws.r + o, perm);
+        permute_row<RP>(ws.s64 + o, perm);
+        permute_row<RP>(ws.beta + o, perm);
+        permute_row<RP>(ws.m + o, perm);
+        permute_row<RP>(ws.dg + o, perm);
+        permute_row<RP>(ws.s32 + o, perm);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const size_t o = (size_t)i * RP;
+        permute_row<RP>(ws.om32 + o, perm);
+        permute_row<RP>(ws.om64 + o, perm);
+    }
+}
+
 // interleaved beta -> caller's chain-major beta
-__global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restrict__ beta) {
+__global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restrict__ beta,
+                        const int *__restrict__ flags) {
     const int64_t p = d->p;
     const int R = d->R, RP = d->RP;
     const int64_t total = p * R;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(t / p);
-        const int64_t j = t - (int64_t)r * p;
-        d->beta_out[t] = beta[j * RP + r];
+        const int s = (int)(t / p);
+        const int64_t j = t - (int64_t)s * p;
+        d->beta_out[(int64_t)flags[32 + s] * p + j] = beta[j * RP + s];
     }
 }
 
@@ -562,33 +716,49 @@ __global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restric
 // ===========================================================================
 
 static cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps,
-                            size_t ndeps, void *func, int grid, int block, void **args) {
+                            size_t ndeps, void *func, int grid, int block, void **args,
+                            size_t smem = 0) {
     cudaKernelNodeParams kp = {};
     kp.func = func;
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(block);
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
 
 struct BatchKernels {
-    void *init, *csr, *csr64, *csc, *update, *true_resid, *sdir;
+    void *init, *csr, *csr64, *csc, *fin, *update, *true_resid, *sdir, *cplan, *capply;
 };
 
 template <int RP>
-static BatchKernels batch_kernels() {
-    return {(void *)k_b_init<RP>, (void *)k_b_csr<RP>, (void *)k_b_csr64<RP>, (void *)k_b_csc<RP>,
-            (void *)k_b_update<RP>, (void *)k_b_true_resid<RP>, (void *)k_b_sdir<RP>};
+static BatchKernels batch_kernels(bool df) {
+    return {(void *)k_b_init<RP>,         (void *)k_b_csr<RP>,          (void *)k_b_csr64<RP>,
+            (void *)k_b_csc<RP>,
+            df ? (void *)k_b_fin<RP, double> : (void *)k_b_fin<RP, float>,
+            (void *)k_b_update<RP>,
+            (void *)k_b_true_resid<RP>,   (void *)k_b_sdir<RP>,         (void *)k_b_compact_plan<RP>,
+            (void *)k_b_compact_apply<RP>};
 }
 
-static BatchKernels kernels_for(int RP) {
+static BatchKernels kernels_for(int RP, bool df = false) {
     switch (RP) {
-        case 4: return batch_kernels<4>();
-        case 8: return batch_kernels<8>();
-        case 16: return batch_kernels<16>();
-        default: return batch_kernels<32>();
+        case 4: return batch_kernels<4>(df);
+        case 8: return batch_kernels<8>(df);
+        case 16: return batch_kernels<16>(df);
+        default: return batch_kernels<32>(df);
     }
 }
+
+// How the products of one iteration run: untiled (RG = 0) or tiled in
+// RP / RG groups of RG right-hand sides.
+struct BatchProducts {
+    int RG = 0;
+    bool df = false;           // double-float products (sources s64 / om64, double partials)
+    TiledPlan plan{};
+    TiledKernels tk{};
+    void *pc_all = nullptr;    // [T_r][p][RP] partials (float, or double with df)
+};
 
 struct BatchNodeArgs {
     const BatchDesc *d;
@@ -604,12 +774,49 @@ struct BatchNodeArgs {
     const int *flag0;
     const int *flags;
     cudaGraphConditionalHandle h_while, h_ru;
-    int one, use_ru;
+    int one, zero, use_ru, RPv, T_r;
+    TiledArgs ta;
+    void *pc_all;
+    const void *s_src, *om_src;
+    int goff[kMaxBatch];
+    const int *ggate[kMaxBatch];   // per product group: skip when flags[96 + g] != 0
 };
 
+// Adds the products of one iteration to `body` after `dep`; returns the last node.
+static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, int ndep,
+                                BatchNodeArgs &A, const BatchKernels &K, const BatchProducts &bp,
+                                int RP, int grid, int gvec, cudaGraphNode_t *last) {
+    cudaError_t e = cudaSuccess;
+    if (bp.RG == 0) {
+        cudaGraphNode_t n1;
+        void *a1[] = {&A.d, &A.s32, &A.om32, &A.u32, &A.flag0};
+        e = add_node(body, &n1, dep, ndep, K.csr, grid, 256, a1);
+        if (e != cudaSuccess) return e;
+        void *a2[] = {&A.d, &A.u32, &A.ws};
+        return add_node(body, last, &n1, 1, K.csc, grid, 256, a2);
+    }
+    const TiledPlan &P = bp.plan;
+    cudaGraphNode_t prev = dep ? *dep : nullptr;
+    int nprev = dep ? ndep : 0;
+    for (int g = 0; g < RP / bp.RG; ++g) {
+        cudaGraphNode_t nc, nr;
+        void *a1[] = {&A.ta, &A.s_src, &A.RPv, &A.goff[g], &A.ggate[g], &A.zero};
+        e = add_node(body, &nc, nprev ? &prev : nullptr, nprev, bp.tk.csr, P.T_c * P.csr_blocks, P.threads,
+                     a1, P.smem_c);
+        if (e != cudaSuccess) return e;
+        void *a2[] = {&A.ta, &A.om_src, &A.RPv, &A.goff[g], &A.pc_all, &A.RPv, &A.goff[g], &A.ggate[g], &A.zero};
+        e = add_node(body, &nr, &nc, 1, bp.tk.csc, P.T_r * P.csc_chunks, P.threads, a2, P.smem_r);
+        if (e != cudaSuccess) return e;
+        prev = nr;
+        nprev = 1;
+    }
+    void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.ws};
+    return add_node(body, last, &prev, 1, K.fin, gvec, 256, a3);
+}
+
 static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, bool refined,
-                                    cudaGraphExec_t *out) {
-    const BatchKernels K = kernels_for(RP);
+                                    const BatchProducts &bp, cudaGraphExec_t *out) {
+    const BatchKernels K = kernels_for(RP, bp.df);
     const int grid = grid_for(ctx, 256, 8);
     const int gvec = grid_for(ctx, 256, 4);
     BatchNodeArgs A{};
@@ -626,11 +833,22 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
     A.flag0 = ws.flags;
     A.flags = ws.flags;
     A.one = 1;
+    A.zero = 0;
     A.use_ru = refined ? 1 : 0;
+    A.RPv = RP;
+    A.ta.plan = bp.plan;
+    A.pc_all = bp.pc_all;
+    A.s_src = bp.df ? (const void *)ws.s64 : (const void *)ws.s32;
+    A.om_src = bp.df ? (const void *)ws.om64 : (const void *)ws.om32;
+    A.T_r = bp.plan.T_r;
+    for (int g = 0; g < kMaxBatch; ++g) {
+        A.goff[g] = g * (bp.RG > 0 ? bp.RG : 1);
+        A.ggate[g] = ws.flags + 96 + g;
+    }
     cudaGraph_t g = nullptr;
     PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
     cudaError_t e;
-    cudaGraphNode_t n_prep, n_init, n_while, n_csr, n_csc, n_upd, n_if, n_sdir, n_r1, n_r2, n_out;
+    cudaGraphNode_t n_prep, n_init, n_while, n_prod, n_upd, n_if, n_sdir, n_r1, n_r2, n_out;
     {
         void *a[] = {&A.d, &A.w64, &A.om64, &A.om32};
         e = add_node(g, &n_prep, nullptr, 0, (void *)k_b_prep, grid, 256, a);
@@ -650,18 +868,11 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
         e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) {
-        void *a[] = {&A.d, &A.s32, &A.om32, &A.u32, &A.flag0};
-        e = add_node(body, &n_csr, nullptr, 0, K.csr, grid, 256, a);
-    }
-    if (e == cudaSuccess) {
-        void *a[] = {&A.d, &A.u32, &A.ws};
-        e = add_node(body, &n_csc, &n_csr, 1, K.csc, grid, 256, a);
-    }
+    if (e == cudaSuccess) e = add_products(body, nullptr, 0, A, K, bp, RP, grid, gvec, &n_prod);
     if (e == cudaSuccess && refined) e = cudaGraphConditionalHandleCreate(&A.h_ru, body, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
         void *a[] = {&A.d, &A.ws, &A.h_ru, &A.use_ru};
-        e = add_node(body, &n_upd, &n_csc, 1, K.update, gvec, 256, a);
+        e = add_node(body, &n_upd, &n_prod, 1, K.update, gvec, 256, a);
     }
     cudaGraphNode_t last = n_upd;
     if (e == cudaSuccess && refined) {
@@ -686,8 +897,14 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
         void *a[] = {&A.d, &A.ws, &A.h_while, &A.one};
         e = add_node(body, &n_sdir, &last, 1, K.sdir, gvec, 256, a);
     }
+    if (e == cudaSuccess && bp.RG > 0) {
+        cudaGraphNode_t n_cp, n_ca;
+        void *a1[] = {&A.d, &A.ws};
+        e = add_node(body, &n_cp, &n_sdir, 1, K.cplan, 1, 32, a1);
+        if (e == cudaSuccess) e = add_node(body, &n_ca, &n_cp, 1, K.capply, gvec, 256, a1);
+    }
     if (e == cudaSuccess) {
-        void *a[] = {&A.d, &A.beta};
+        void *a[] = {&A.d, &A.beta, &A.flags};
         e = add_node(g, &n_out, &n_while, 1, (void *)k_b_out, gvec, 256, a);
     }
     if (e != cudaSuccess) {
@@ -703,16 +920,44 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
 }
 
 template <int RP>
-static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refined, int grid, int gvec) {
+static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refined, int grid, int gvec,
+                                    const BatchProducts &bp) {
     cudaStream_t st = ctx->stream;
-    PCG_PROF(ctx, "b_csr_f32", k_b_csr<RP><<<grid, 256, 0, st>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, ws.flags));
-    PCG_PROF(ctx, "b_csc_f32", k_b_csc<RP><<<grid, 256, 0, st>>>(ws.desc, (const float *)ws.u, ws));
+    if (bp.RG == 0) {
+        PCG_PROF(ctx, "b_csr_f32", k_b_csr<RP><<<grid, 256, 0, st>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, ws.flags));
+        PCG_PROF(ctx, "b_csc_f32", k_b_csc<RP><<<grid, 256, 0, st>>>(ws.desc, (const float *)ws.u, ws));
+    } else {
+        const TiledPlan &P = bp.plan;
+        TiledArgs ta{P};
+        int rp = RP, zero = 0, T_r = P.T_r;
+        const void *s32 = bp.df ? (const void *)ws.s64 : (const void *)ws.s32;
+        const void *om32 = bp.df ? (const void *)ws.om64 : (const void *)ws.om32;
+        void *pc = bp.pc_all;
+        const int *flags = ws.flags;
+        const BatchDesc *dd = ws.desc;
+        BatchWs wsv = ws;
+        for (int g = 0; g < RP / bp.RG; ++g) {
+            int off = g * bp.RG;
+            const int *gate = flags + 96 + g;
+            void *a1[] = {&ta, (void *)&s32, &rp, &off, (void *)&gate, &zero};
+            void *a2[] = {&ta, (void *)&om32, &rp, &off, &pc, &rp, &off, (void *)&gate, &zero};
+            PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, dim3(P.T_c * P.csr_blocks), dim3(P.threads), a1, P.smem_c, st));
+            PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, dim3(P.T_r * P.csc_chunks), dim3(P.threads), a2, P.smem_r, st));
+        }
+        void *a3[] = {(void *)&dd, &pc, &T_r, &wsv};
+        PCG_PROF(ctx, "bt_fin", cudaLaunchKernel(bp.df ? (void *)k_b_fin<RP, double> : (void *)k_b_fin<RP, float>,
+                                                 dim3(gvec), dim3(256), a3, 0, st));
+    }
     PCG_PROF(ctx, "b_update", k_b_update<RP><<<gvec, 256, 0, st>>>(ws.desc, ws, 0, 0));
     if (refined) {
         PCG_PROF(ctx, "b_ru_csr_f64", k_b_csr64<RP><<<grid, 256, 0, st>>>(ws.desc, ws.beta, ws.om64, (double *)ws.u, ws.flags));
         PCG_PROF(ctx, "b_ru_true_resid", k_b_true_resid<RP><<<grid, 256, 0, st>>>(ws.desc, (const double *)ws.u, ws));
     }
     PCG_PROF(ctx, "b_sdir", k_b_sdir<RP><<<gvec, 256, 0, st>>>(ws.desc, ws, 0, 0));
+    if (bp.RG > 0) {
+        PCG_PROF(ctx, "b_compact_plan", k_b_compact_plan<RP><<<1, 32, 0, st>>>(ws.desc, ws));
+        PCG_PROF(ctx, "b_compact_apply", k_b_compact_apply<RP><<<gvec, 256, 0, st>>>(ws.desc, ws));
+    }
 }
 
 template <int RP>
@@ -721,10 +966,195 @@ static void launch_batch_plain_init(pcg_ctx *ctx, const BatchWs &ws, int grid) {
     PCG_PROF(ctx, "b_init", k_b_init<RP><<<grid, 256, 0, ctx->stream>>>(ws.desc, (const double *)ws.u, ws));
 }
 
+// Tiled products for a group width RG (0: untiled).
+static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int RP, int RG,
+                                BatchProducts *bp) {
+    *bp = BatchProducts{};
+    const bool df = ctx->opt.precision == PCG_PREC_DF32;
+    if ((RG == 0 || !ctx->tiled_enabled) && !df) return PCG_OK;
+    if (RG == 0) RG = 1;   // double-float products exist only in tiled form
+    char tag[32];
+    snprintf(tag, sizeof tag, "batch%d%s", RG, df ? "d" : "");
+    pcg_status st = build_tiled_plan(ctx, tag, Xr, Xc, RG, df ? kVtDF : kVtF32, &bp->plan);
+    if (st != PCG_OK) return st;
+    if (!bp->plan.valid) return PCG_OK;
+    st = tiled_prepare(ctx, bp->plan, &bp->tk);
+    if (st != PCG_OK) return st;
+    cudaError_t e;
+    bp->pc_all = grow(ctx, std::string(tag) + ":pc_all",
+                      (df ? sizeof(double) : sizeof(float)) * (size_t)bp->plan.T_r * bp->plan.p * RP, &e);
+    if (!bp->pc_all) return cuda_error(ctx, e, "allocating the batched partials");
+    bp->RG = RG;
+    bp->df = df;
+    return PCG_OK;
+}
+
+static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool refined, int nrhs,
+                               int max_iter, const BatchProducts &bp, CgScalars *hsc, int *hflags) {
+    const int grid = grid_for(ctx, 256, 8), gvec = grid_for(ctx, 256, 4);
+    cudaError_t e;
+    if (ctx->opt.use_graph && !ctx->opt.profile) {
+        char key[256];
+        snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p|%d%s:%d:%d:%d:%d:%d:%d:%lld:%lld:%p:%p:%p:%p:%p:%p",
+                 RP, (int)refined, grid, gvec, (void *)ws.b, ws.u, (void *)ws.om64, (void *)ws.om32, bp.RG, bp.df ? "d" : "",
+                 bp.plan.T_c, bp.plan.T_r, bp.plan.csr_blocks, bp.plan.csc_chunks,
+                 bp.plan.G_row * 64 + bp.plan.G_col, bp.plan.threads, (long long)bp.plan.n,
+                 (long long)bp.plan.p, (void *)bp.plan.col16, (void *)bp.plan.row16, (void *)bp.plan.rt,
+                 (void *)bp.plan.cs, bp.plan.Pr, (void *)bp.pc_all);
+        auto it = ctx->named_graphs.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (it == ctx->named_graphs.end()) {
+            pcg_status st = build_batch_graph(ctx, ws, RP, refined, bp, &exec);
+            if (st != PCG_OK) return st;
+            ctx->named_graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+        PCG_CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, sizeof(int) * kFlagInts, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        // graph nodes that ran: prep, init and the output transpose; per loop
+        // trip (at least one) the products, update and direction; 2 per
+        // float64 recomputation of r
+        int trips = 1;
+        for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
+        const int per_trip = (bp.RG ? 2 * (RP / bp.RG) + 1 + 2 : 2) + 2;
+        ctx->last_launches += 3 + (int64_t)per_trip * trips + 2 * (int64_t)hflags[2];
+        return PCG_OK;
+    }
+    switch (RP) {
+        case 4: launch_batch_plain_init<4>(ctx, ws, grid); break;
+        case 8: launch_batch_plain_init<8>(ctx, ws, grid); break;
+        case 16: launch_batch_plain_init<16>(ctx, ws, grid); break;
+        default: launch_batch_plain_init<32>(ctx, ws, grid); break;
+    }
+    for (int it = 0;; it += 8) {
+        for (int k = 0; k < 8; ++k) {
+            switch (RP) {
+                case 4: launch_batch_plain_iter<4>(ctx, ws, refined, grid, gvec, bp); break;
+                case 8: launch_batch_plain_iter<8>(ctx, ws, refined, grid, gvec, bp); break;
+                case 16: launch_batch_plain_iter<16>(ctx, ws, refined, grid, gvec, bp); break;
+                default: launch_batch_plain_iter<32>(ctx, ws, refined, grid, gvec, bp); break;
+            }
+        }
+        PCG_CUDA_TRY(ctx, cudaGetLastError());
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, sizeof(int) * kFlagInts, cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        prof_collect(ctx);
+        if (hflags[0]) break;
+        if (it > max_iter + 16) return set_error(ctx, PCG_TIMEOUT, "host loop ran past max_iter");
+    }
+    PCG_PROF(ctx, "b_out", k_b_out<<<gvec, 256, 0, ctx->stream>>>(ws.desc, ws.beta, ws.flags));
+    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, sizeof(int) * kFlagInts, cudaMemcpyDeviceToHost, ctx->stream));
+    PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+    return PCG_OK;
+}
+
+// RHS-group width for this design and block: cached per (n, p, nnz, RP)
+// in the context and the autotune file; otherwise every candidate runs a few
+// iterations and the fastest per iteration wins.
+static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const BatchWs &ws,
+                            BatchDesc &d, BatchDesc *hd, int RP, bool refined, int nrhs,
+                            CgScalars *hsc, int *hflags, int *rg_out) {
+    // PCG_BETA_BATCH_RG in the environment forces the width (tests use it to
+    // cover every width); 0 selects the untiled products
+    const char *force = getenv("PCG_BETA_BATCH_RG");
+    if (force && force[0]) {
+        const int v = atoi(force);
+        *rg_out = (v == 1 || v == 2 || v == 4 || v == 8) && v <= RP ? v : 0;
+        if (ctx->opt.precision == PCG_PREC_DF32 && (*rg_out == 0 || *rg_out > 4)) *rg_out = 4 <= RP ? 4 : RP;
+        return PCG_OK;
+    }
+    char key[128];
+    snprintf(key, sizeof key, "batch_rg:%lld:%lld:%lld:%d", (long long)Xr->n, (long long)Xr->p,
+             (long long)Xr->nnz, RP);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end() && !it->second.empty()) {
+        *rg_out = it->second[0];
+        return PCG_OK;
+    }
+    if (ctx->opt.autotune_cache) {
+        FILE *f = fopen(ctx->opt.autotune_cache, "r");
+        if (f) {
+            char k[128];
+            int v;
+            while (fscanf(f, "%127s %d%*[^\n]", k, &v) == 2) {
+                if (strcmp(k, key) == 0) {
+                    fclose(f);
+                    ctx->tuned[key] = {v};
+                    *rg_out = v;
+                    return PCG_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    int best_rg = 0;
+    if (ctx->tiled_enabled) {
+        const int saved_iter = d.max_iter;
+        const double saved_tol = d.tol;
+        d.max_iter = 12;   // a short, fixed number of iterations per candidate
+        d.tol = 0.0;
+        *hd = d;
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
+        float best = 1e30f;
+        const int cands[] = {0, 1, 2, 4, 8};
+        const bool df = ctx->opt.precision == PCG_PREC_DF32;
+        for (int rg : cands) {
+            if (rg > RP || (df && (rg == 0 || rg > 4))) continue;
+            BatchProducts bp;
+            pcg_status st = make_products(ctx, Xr, Xc, RP, rg, &bp);
+            if (st != PCG_OK) return st;
+            if (rg && !bp.RG) continue;
+            d.RG = bp.RG;
+            *hd = d;
+            PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run builds the graph
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, ctx->stream);
+                st = batched_once(ctx, ws, RP, refined, nrhs, 12, bp, hsc, hflags);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (st != PCG_OK) return st;
+            }
+            if (ms < best) {
+                best = ms;
+                best_rg = rg;
+            }
+        }
+        d.max_iter = saved_iter;
+        d.tol = saved_tol;
+        *hd = d;
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->tuned[key] = {best_rg};
+    if (ctx->opt.autotune_cache) {
+        FILE *f = fopen(ctx->opt.autotune_cache, "a");
+        if (f) {
+            fprintf(f, "%s %d\n", key, best_rg);
+            fclose(f);
+        }
+    }
+    *rg_out = best_rg;
+    return PCG_OK;
+}
+
 pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int nrhs,
                        const double *omega, const double *z, const double *lambda,
                        const double *tau, const double *eta, const double *delta, double tol,
                        int max_iter, double *beta, int *iters, double *resid, int *status) {
+    if (ctx->opt.precision == PCG_PREC_FP64)
+        return set_error(ctx, PCG_BADARG, "the batched path computes its products in float32 arithmetic: use PCG_PREC_FP32_REFINED, PCG_PREC_FP32 or PCG_PREC_DF32");
     int RP = 4;
     while (RP < nrhs) RP *= 2;
     const int64_t n = std::max<int64_t>(Xr->n, 1), p = std::max<int64_t>(Xr->p, 1);
@@ -734,10 +1164,10 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     // one block for the p-sized vectors and the small state
     const size_t total_p = 7 * up(vp) + up(sizeof(float) * (size_t)p * RP) +
                            up(sizeof(double) * kMaxReduceBlocks * 32) + up(64 * sizeof(unsigned)) +
-                           up(sizeof(CgScalars) * kMaxBatch) + up(64) + up(sizeof(BatchDesc));
+                           up(sizeof(CgScalars) * kMaxBatch) + up(sizeof(int) * kFlagInts) + up(sizeof(BatchDesc));
     cudaError_t e;
-    char *bp = (char *)grow(ctx, "batch_p", total_p, &e);
-    if (!bp) return cuda_error(ctx, e, "allocating the batched workspace");
+    char *bp_mem = (char *)grow(ctx, "batch_p", total_p, &e);
+    if (!bp_mem) return cuda_error(ctx, e, "allocating the batched workspace");
     void *bu = grow(ctx, "batch_u", sizeof(double) * (size_t)n * RP, &e);
     if (!bu) return cuda_error(ctx, e, "allocating the batched workspace");
     double *bom64 = (double *)grow(ctx, "batch_om64", sizeof(double) * (size_t)n * RP, &e);
@@ -746,7 +1176,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     if (!bom32) return cuda_error(ctx, e, "allocating the batched workspace");
     BatchWs ws{};
     size_t off = 0;
-    auto take = [&](size_t sz) { char *q = bp + off; off += up(sz); return q; };
+    auto take = [&](size_t sz) { char *q = bp_mem + off; off += up(sz); return q; };
     ws.b = (double *)take(vp);
     ws.r = (double *)take(vp);
     ws.s64 = (double *)take(vp);
@@ -758,7 +1188,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     ws.partials = (double *)take(sizeof(double) * kMaxReduceBlocks * 32);
     ws.counters = (unsigned *)take(64 * sizeof(unsigned));
     ws.sc = (CgScalars *)take(sizeof(CgScalars) * kMaxBatch);
-    ws.flags = (int *)take(64);
+    ws.flags = (int *)take(sizeof(int) * kFlagInts);
     ws.desc = (BatchDesc *)take(sizeof(BatchDesc));
     ws.u = bu;
     ws.om64 = bom64;
@@ -768,7 +1198,8 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
 
     BatchDesc *hd = (BatchDesc *)grow_host(ctx, "batch_desc", sizeof(BatchDesc), &e);
     CgScalars *hsc = (CgScalars *)grow_host(ctx, "batch_sc", sizeof(CgScalars) * kMaxBatch, &e);
-    if (!hd || !hsc) return cuda_error(ctx, e, "allocating pinned staging");
+    int *hflags = (int *)grow_host(ctx, "batch_flags", sizeof(int) * kFlagInts, &e);
+    if (!hd || !hsc || !hflags) return cuda_error(ctx, e, "allocating pinned staging");
     BatchDesc d{};
     d.row_ptr = Xr->row_ptr;
     d.col_idx = Xr->col_idx;
@@ -791,72 +1222,25 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     d.stop_rule = ctx->opt.stop_rule;
     d.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
+    const bool refined = d.refined != 0;
+    int RG = 0;
+    pcg_status st = choose_rg(ctx, Xr, Xc, ws, d, hd, RP, refined, nrhs, hsc, hflags, &RG);
+    if (st != PCG_OK) return st;
+    BatchProducts bp;
+    st = make_products(ctx, Xr, Xc, RP, RG, &bp);
+    if (st != PCG_OK) return st;
+    ctx->last_launches = 0;
+    d.RG = bp.RG;
     *hd = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
-    if (ctx->opt.precision == PCG_PREC_FP64)
-        return set_error(ctx, PCG_BADARG, "the batched path computes its products in float32: use PCG_PREC_FP32_REFINED or PCG_PREC_FP32");
-    const bool refined = d.refined != 0;
-    const int grid = grid_for(ctx, 256, 8), gvec = grid_for(ctx, 256, 4);
-    int *hflags_g = (int *)grow_host(ctx, "batch_flags_g", 64, &e);
-    if (!hflags_g) return cuda_error(ctx, e, "allocating pinned staging");
-    if (ctx->opt.use_graph && !ctx->opt.profile) {
-        char key[160];
-        snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p", RP, (int)refined, grid, gvec,
-                 (void *)bp, bu, (void *)bom64, (void *)bom32);
-        auto it = ctx->named_graphs.find(key);
-        cudaGraphExec_t exec = nullptr;
-        if (it == ctx->named_graphs.end()) {
-            pcg_status st = build_batch_graph(ctx, ws, RP, refined, &exec);
-            if (st != PCG_OK) return st;
-            ctx->named_graphs[key] = exec;
-        } else {
-            exec = it->second;
-        }
-        PCG_CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
-        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags_g, ws.flags, 64, cudaMemcpyDeviceToHost, ctx->stream));
-        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        // graph nodes that ran: prep, init and the output transpose, 4 per loop
-        // trip (at least one), 2 per float64 recomputation of r
-        int trips = 1;
-        for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
-        ctx->last_launches += 3 + 4 * (int64_t)trips + 2 * (int64_t)hflags_g[2];
-    } else {
-        switch (RP) {
-            case 4: launch_batch_plain_init<4>(ctx, ws, grid); break;
-            case 8: launch_batch_plain_init<8>(ctx, ws, grid); break;
-            case 16: launch_batch_plain_init<16>(ctx, ws, grid); break;
-            default: launch_batch_plain_init<32>(ctx, ws, grid); break;
-        }
-        int *hflags = (int *)grow_host(ctx, "batch_flags", 64, &e);
-        if (!hflags) return cuda_error(ctx, e, "allocating pinned staging");
-        for (int it = 0;; it += 8) {
-            for (int k = 0; k < 8; ++k) {
-                switch (RP) {
-                    case 4: launch_batch_plain_iter<4>(ctx, ws, refined, grid, gvec); break;
-                    case 8: launch_batch_plain_iter<8>(ctx, ws, refined, grid, gvec); break;
-                    case 16: launch_batch_plain_iter<16>(ctx, ws, refined, grid, gvec); break;
-                    default: launch_batch_plain_iter<32>(ctx, ws, refined, grid, gvec); break;
-                }
-            }
-            PCG_CUDA_TRY(ctx, cudaGetLastError());
-            PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, 64, cudaMemcpyDeviceToHost, ctx->stream));
-            PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-            prof_collect(ctx);
-            if (hflags[0]) break;
-            if (it > max_iter + 16) return set_error(ctx, PCG_TIMEOUT, "host loop ran past max_iter");
-        }
-        PCG_PROF(ctx, "b_out", k_b_out<<<gvec, 256, 0, ctx->stream>>>(ws.desc, ws.beta));
-        PCG_CUDA_TRY(ctx, cudaGetLastError());
-        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hsc, ws.sc, sizeof(CgScalars) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        prof_collect(ctx);
-    }
+    st = batched_once(ctx, ws, RP, refined, nrhs, max_iter, bp, hsc, hflags);
+    if (st != PCG_OK) return st;
     pcg_status worst = PCG_OK;
-    for (int r = 0; r < nrhs; ++r) {
-        iters[r] = hsc[r].iter;
-        resid[r] = hsc[r].resid;
-        status[r] = hsc[r].status == kRunning ? PCG_TIMEOUT : hsc[r].status;
+    for (int s = 0; s < nrhs; ++s) {   // slot s holds chain flags[32 + s] after compactions
+        const int r = hflags[32 + s];
+        iters[r] = hsc[s].iter;
+        resid[r] = hsc[s].resid;
+        status[r] = hsc[s].status == kRunning ? PCG_TIMEOUT : hsc[s].status;
         if (status[r] > worst) worst = (pcg_status)status[r];
     }
     if (worst != PCG_OK) return set_error(ctx, worst, "at least one chain did not converge (see status[])");

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -223,12 +224,14 @@ pcg_status pcg_ctx_create(pcg_ctx **out, const pcg_options *opt, void *stream) {
     pcg_ctx *ctx = new pcg_ctx();
     if (opt) ctx->opt = *opt;
     else pcg_options_default(&ctx->opt);
-    if (ctx->opt.precision < 0 || ctx->opt.precision > 2 || ctx->opt.stop_rule < 0 ||
+    if (ctx->opt.precision < 0 || ctx->opt.precision > 3 || ctx->opt.stop_rule < 0 ||
         ctx->opt.stop_rule > 1 || ctx->opt.reliable_k < 0) {
         delete ctx;
         return PCG_BADARG;
     }
     ctx->stream = (cudaStream_t)stream;
+    const char *tiled = getenv("PCG_BETA_TILED");
+    ctx->tiled_enabled = !(tiled && tiled[0] == '0');
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);

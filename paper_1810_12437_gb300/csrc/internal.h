@@ -60,6 +60,7 @@ struct SingleWs {
     float *s32;                   // p
     void *u;                      // n doubles (aliased as n floats in FP32 modes)
     float *om32;                  // n
+    double *om64;                 // n (float64 omega for the tiled float64 products)
     double *partials;             // kMaxReduceBlocks * 4
     unsigned int *counters;       // 16
     CgScalars *sc;                // 1
@@ -117,6 +118,8 @@ struct pcg_ctx {
     std::map<std::string, std::pair<double, int64_t>> prof;
     std::vector<std::string> prof_names;
     int64_t last_launches = 0;
+    // shared-memory tiled products (on unless PCG_BETA_TILED=0 in the environment)
+    bool tiled_enabled = true;
 };
 
 namespace pcg {

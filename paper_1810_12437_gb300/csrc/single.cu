@@ -20,6 +20,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "tiled.h"
 
 namespace pcg {
 
@@ -52,7 +53,8 @@ __device__ __forceinline__ bool gate_closed(const int *done, const int *need) {
 // of omega used by the float32 products.
 // ---------------------------------------------------------------------------
 __global__ void k_rhs_w(const DrawDesc *__restrict__ d, double *__restrict__ w,
-                        float *__restrict__ om32, int want_w, int want_om32) {
+                        float *__restrict__ om32, int want_w, int want_om32,
+                        double *__restrict__ om64) {
     const int64_t n = d->n;
     const double *__restrict__ om = d->omega;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -60,6 +62,22 @@ __global__ void k_rhs_w(const DrawDesc *__restrict__ d, double *__restrict__ w,
         const double o = om[i];
         if (want_w) w[i] = o * d->z[i] + sqrt(o) * d->eta[i];
         if (want_om32) om32[i] = (float)o;
+        if (om64) om64[i] = o;
+    }
+}
+
+// out = sum_t Pc[t] + d v (pcg_phi_mul through the tiled products)
+template <typename T>
+__global__ void k_t_fin_out(const DrawDesc *__restrict__ d, TiledArgs A, const double *__restrict__ v,
+                            double *__restrict__ out) {
+    const TiledPlan &P = A.plan;
+    const int64_t p = d->p;
+    const T *__restrict__ Pc = reinterpret_cast<const T *>(P.Pc);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        T acc = Pc[j];
+        for (int t = 1; t < P.T_r; ++t) acc += Pc[(size_t)t * p + j];
+        out[j] = (double)acc + prior_prec(d->tau, d->lambda[j]) * v[j];
     }
 }
 
@@ -452,9 +470,9 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
     const size_t szp64 = up(sizeof(double) * cp), szp32 = up(sizeof(float) * cp);
-    const size_t szn32 = up(sizeof(float) * cn);
+    const size_t szn32 = up(sizeof(float) * cn), szn64 = up(sizeof(double) * cn);
     const size_t szpart = up(sizeof(double) * kMaxReduceBlocks * 4);
-    const size_t total = 4 * szp64 + szp32 + szn32 + szpart + up(64 * sizeof(unsigned)) +
+    const size_t total = 4 * szp64 + szp32 + szn32 + szn64 + szpart + up(64 * sizeof(unsigned)) +
                          up(sizeof(CgScalars)) + up(sizeof(DrawDesc));
     char *base = nullptr;
     PCG_CUDA_TRY(ctx, cudaMalloc(&base, total));
@@ -468,6 +486,7 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     w.v64 = (double *)take(szp64);
     w.s32 = (float *)take(szp32);
     w.om32 = (float *)take(szn32);
+    w.om64 = (double *)take(szn64);
     w.partials = (double *)take(szpart);
     w.counters = (unsigned *)take(up(64 * sizeof(unsigned)));
     w.sc = (CgScalars *)take(up(sizeof(CgScalars)));
@@ -501,12 +520,13 @@ static SingleLaunch single_launch(pcg_ctx *ctx, const DrawDesc &d) {
 
 // Adds one kernel node; args is the kernel's argument pointer array.
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps,
-                              size_t ndeps, void *func, int grid, int block, void **args) {
+                              size_t ndeps, void *func, int grid, int block, void **args,
+                              size_t smem = 0) {
     cudaKernelNodeParams kp = {};
     kp.func = func;
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(block);
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     kp.extra = nullptr;
     return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
@@ -524,11 +544,24 @@ struct NodeArgs {
     const int *done, *nulli;
     cudaGraphConditionalHandle h_ru, h_while;
     int one, zero, want_w, want_om32, use_cond_ru;
+    TiledArgs ta;
+    double *om64;
+    const void *om_t;
+    void *pc;
 };
 
-static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cudaGraphExec_t *out) {
+static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, const TiledPlan &tp,
+                              cudaGraphExec_t *out) {
     const SingleLaunch L = single_launch(ctx, d);
-    const bool f32 = precision != PCG_PREC_FP64;
+    const bool tiled = tp.valid;
+    // float32 gathers in the FP32 modes; float64 sources (s64, omega) in the
+    // FP64 and DF32 modes (the DF32 tiled kernels split them on staging)
+    TiledKernels TK{};
+    if (tiled) {
+        pcg_status st = tiled_prepare(ctx, tp, &TK);
+        if (st != PCG_OK) return st;
+    }
+    const bool f32 = precision == PCG_PREC_FP32 || precision == PCG_PREC_FP32_REFINED;
     const bool refined = d.refined != 0;
     NodeArgs A{};
     A.d = ctx->ws.desc;
@@ -549,6 +582,10 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cu
     A.one = 1;
     A.zero = 0;
     A.use_cond_ru = refined ? 1 : 0;
+    A.ta.plan = tp;
+    A.om64 = (tiled && !f32) ? ctx->ws.om64 : nullptr;
+    A.om_t = f32 ? (const void *)ctx->ws.om32 : (const void *)ctx->ws.om64;
+    A.pc = tp.Pc;
 
     cudaGraph_t g = nullptr;
     PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
@@ -556,7 +593,7 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cu
     cudaGraphNode_t n_w, n_init, n_while, n_csr, n_csc, n_upd, n_if, n_sdir, n_rcsr, n_tr;
     cudaGraph_t body = nullptr;
     {
-        void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32};
+        void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32, &A.om64};
         e = add_kernel(g, &n_w, nullptr, 0, (void *)k_rhs_w, L.grid_stream, L.threads, args);
     }
     if (e == cudaSuccess) {
@@ -574,17 +611,30 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cu
         e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && tiled) {
+        // tiled products: CSR tiles -> CSC strips -> finalize (sigma, alpha)
+        cudaGraphNode_t n_tc;
+        void *a1[] = {&A.ta, &A.s_gather, &A.one, &A.zero, &A.done, &A.zero};
+        e = add_kernel(body, &n_csr, nullptr, 0, TK.csr, tp.T_c * tp.csr_blocks, tp.threads, a1, tp.smem_c);
+        if (e == cudaSuccess) {
+            void *a2[] = {&A.ta, &A.om_t, &A.one, &A.zero, &A.pc, &A.one, &A.zero, &A.done, &A.zero};
+            e = add_kernel(body, &n_tc, &n_csr, 1, TK.csc, tp.T_r * tp.csc_chunks, tp.threads, a2, tp.smem_r);
+        }
+        if (e == cudaSuccess) {
+            void *a3[] = {&A.d, &A.ta, &A.ws};
+            e = add_kernel(body, &n_csc, &n_tc, 1, TK.fin1, L.grid_vec, L.threads, a3);
+        }
+    } else if (e == cudaSuccess) {
         void *args[] = {&A.d, &A.s_gather, &A.om, &A.u, &A.done, &A.nulli};
         e = add_kernel(body, &n_csr, nullptr, 0,
                        f32 ? csr_kernel_ptr<float>(L.G_row) : csr_kernel_ptr<double>(L.G_row),
                        L.grid_stream, L.threads, args);
-    }
-    if (e == cudaSuccess) {
-        void *args[] = {&A.d, &A.u, &A.s64, &A.v64, &A.ws, &A.one};
-        e = add_kernel(body, &n_csc, &n_csr, 1,
-                       f32 ? csc_kernel_ptr<float>(L.G_col) : csc_kernel_ptr<double>(L.G_col),
-                       L.grid_stream, L.threads, args);
+        if (e == cudaSuccess) {
+            void *a2[] = {&A.d, &A.u, &A.s64, &A.v64, &A.ws, &A.one};
+            e = add_kernel(body, &n_csc, &n_csr, 1,
+                           f32 ? csc_kernel_ptr<float>(L.G_col) : csc_kernel_ptr<double>(L.G_col),
+                           L.grid_stream, L.threads, a2);
+        }
     }
     if (e == cudaSuccess && refined)
         e = cudaGraphConditionalHandleCreate(&A.h_ru, body, 0, cudaGraphCondAssignDefault);
@@ -631,19 +681,41 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, cu
 }
 
 // Plain launches (use_graph = 0): same kernels, host check every 8 iterations.
-static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision) {
+static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, const TiledPlan &tp) {
     const SingleLaunch L = single_launch(ctx, d);
-    const bool f32 = precision != PCG_PREC_FP64;
+    const char *csr_name = precision == PCG_PREC_DF32 ? "t_csr_df32" : precision == PCG_PREC_FP64 ? "t_csr_f64" : "t_csr_f32";
+    const char *csc_name = precision == PCG_PREC_DF32 ? "t_csc_df32" : precision == PCG_PREC_FP64 ? "t_csc_f64" : "t_csc_f32";
+    TiledKernels TK{};
+    if (tp.valid) {
+        pcg_status st = tiled_prepare(ctx, tp, &TK);
+        if (st != PCG_OK) return st;
+    }
+    TiledArgs ta{tp};
+    const bool f32 = precision == PCG_PREC_FP32 || precision == PCG_PREC_FP32_REFINED;
     SingleWs ws = ctx->ws;
     const DrawDesc *dd = ws.desc;
     cudaStream_t st = ctx->stream;
     const int B = L.threads;
-    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32));
+    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32,
+                                                                (tp.valid && !f32) ? ws.om64 : nullptr));
     PCG_PROF(ctx, "rhs_init", PCG_DISPATCH_G(L.G_col, (k_rhs_init<GG><<<L.grid_stream, B, 0, st>>>(dd, (const double *)ws.u, ws))));
     const int *done = &ws.sc->done, *need = &ws.sc->need_ru;
     for (int it = 0;; it += 8) {
         for (int k = 0; k < 8; ++k) {
-            if (f32) {
+            if (tp.valid) {
+                const void *sg = f32 ? (const void *)ws.s32 : (const void *)ws.s64;
+                const void *omt = f32 ? (const void *)ws.om32 : (const void *)ws.om64;
+                int one = 1, zero = 0;
+                void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
+                void *pc = tp.Pc;
+                void *a2[] = {&ta, (void *)&omt, &one, &zero, &pc, &one, &zero, (void *)&done, &zero};
+                void *a3[] = {(void *)&dd, &ta, &ws};
+                PCG_PROF(ctx, csr_name,
+                         cudaLaunchKernel(TK.csr, dim3(tp.T_c * tp.csr_blocks), dim3(tp.threads), a1, tp.smem_c, st));
+                PCG_PROF(ctx, csc_name,
+                         cudaLaunchKernel(TK.csc, dim3(tp.T_r * tp.csc_chunks), dim3(tp.threads), a2, tp.smem_r, st));
+                PCG_PROF(ctx, "t_fin", cudaLaunchKernel(TK.fin1, dim3(L.grid_vec), dim3(B), a3, 0, st));
+            } else if (f32) {
                 PCG_PROF(ctx, "csr_f32", PCG_DISPATCH_G(L.G_row, (k_csr<float, GG><<<L.grid_stream, B, 0, st>>>(
                                             dd, ws.s32, ws.om32, (float *)ws.u, done, nullptr))));
                 PCG_PROF(ctx, "csc_f32", PCG_DISPATCH_G(L.G_col, (k_csc<float, GG><<<L.grid_stream, B, 0, st>>>(
@@ -683,20 +755,31 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     *ctx->h_desc = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
                                       cudaMemcpyHostToDevice, ctx->stream));
+    TiledPlan tp{};
+    if (ctx->tiled_enabled) {
+        const pcg_csr xr{d.n, d.p, d.nnz, d.row_ptr, d.col_idx};
+        const pcg_csc xc{d.n, d.p, d.nnz, d.col_ptr, d.row_idx};
+        const int vt = precision == PCG_PREC_FP64 ? kVtF64 : precision == PCG_PREC_DF32 ? kVtDF : kVtF32;
+        st = build_tiled_plan(ctx, "single", &xr, &xc, 1, vt, &tp);
+        if (st != PCG_OK) return st;
+    }
     if (ctx->opt.use_graph && !ctx->opt.profile) {
-        // The graph bakes in the workspace, the group widths and, in the FP64
-        // mode and the refined mode's recomputation, the caller's omega and
-        // beta pointers; those form the cache key.
+        // The graph bakes in the workspace, the plan buffers and the launch
+        // shapes (never a caller pointer: those are read from the descriptor).
         const SingleLaunch L = single_launch(ctx, d);
-        char key[96];
-        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d", L.G_row, L.G_col, L.grid_stream,
-                 L.grid_vec, precision, d.refined, mode);
-        auto it = ctx->named_graphs.find(key);
+        char key[256];
+        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d|%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p",
+                 L.G_row, L.G_col, L.grid_stream, L.grid_vec, precision, d.refined, mode, (int)tp.valid,
+                 tp.W_c, tp.T_c, tp.W_r, tp.T_r, tp.csr_blocks, tp.csc_chunks, tp.G_row * 64 + tp.G_col,
+                 (void *)tp.col16, (void *)tp.row16, (void *)tp.rt, (void *)tp.cs, tp.Pr, tp.Pc);
+        // n and p enter through the plan only when it is valid
+        std::string skey = std::string(key) + (tp.valid ? ":" + std::to_string(tp.n) + ":" + std::to_string(tp.p) : "");
+        auto it = ctx->named_graphs.find(skey);
         cudaGraphExec_t exec = nullptr;
         if (it == ctx->named_graphs.end()) {
-            st = build_graph(ctx, d, precision, &exec);
+            st = build_graph(ctx, d, precision, tp, &exec);
             if (st != PCG_OK) return st;
-            ctx->named_graphs[key] = exec;
+            ctx->named_graphs[skey] = exec;
         } else {
             exec = it->second;
         }
@@ -707,9 +790,9 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         // graph nodes that ran: 2 set-up kernels, 4 per loop trip (at least
         // one trip), 2 per float64 recomputation of r
         const CgScalars &h = *ctx->h_sc;
-        ctx->last_launches += 2 + 4 * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
+        ctx->last_launches += 2 + (tp.valid ? 5 : 4) * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
     } else {
-        st = run_plain(ctx, d, precision);
+        st = run_plain(ctx, d, precision, tp);
         if (st != PCG_OK) return st;
     }
     const CgScalars &sc = *ctx->h_sc;
@@ -747,7 +830,7 @@ pcg_status launch_build_rhs(pcg_ctx *ctx, const pcg_csc *X, const double *omega,
                                       cudaMemcpyHostToDevice, ctx->stream));
     const int grid = std::min(ctx->num_sms * 8, kMaxReduceBlocks);
     const int G = pick_group(d.p > 0 ? (double)d.nnz / d.p : 1.0);
-    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (double *)ctx->ws.u, ctx->ws.om32, 1, 0));
+    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (double *)ctx->ws.u, ctx->ws.om32, 1, 0, nullptr));
     PCG_PROF(ctx, "rhs_b", PCG_DISPATCH_G(G, (k_rhs_b<GG><<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (const double *)ctx->ws.u, b))));
     PCG_CUDA_TRY(ctx, cudaGetLastError());
     PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -781,9 +864,35 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
     const int Gc = pick_group(d.p > 0 ? (double)d.nnz / d.p : 1.0);
     SingleWs ws = ctx->ws;
     const int *done = &ws.sc->done;
-    if (ctx->opt.precision != PCG_PREC_FP64) {
+    const int prec = ctx->opt.precision;
+    const bool f32 = prec == PCG_PREC_FP32 || prec == PCG_PREC_FP32_REFINED;
+    TiledPlan tp{};
+    if (ctx->tiled_enabled) {
+        const int vt = prec == PCG_PREC_FP64 ? kVtF64 : prec == PCG_PREC_DF32 ? kVtDF : kVtF32;
+        pcg_status st2 = build_tiled_plan(ctx, "single", Xr, Xc, 1, vt, &tp);
+        if (st2 != PCG_OK) return st2;
+    }
+    if (tp.valid) {
+        TiledKernels TK{};
+        pcg_status st2 = tiled_prepare(ctx, tp, &TK);
+        if (st2 != PCG_OK) return st2;
+        TiledArgs ta{tp};
+        if (f32) PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
+        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, f32 ? 1 : 0,
+                                                            f32 ? nullptr : ws.om64));
+        const void *sg = f32 ? (const void *)ws.s32 : (const void *)v;
+        const void *omt = f32 ? (const void *)ws.om32 : (const void *)ws.om64;
+        int one = 1, zero = 0;
+        void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
+        void *pc = tp.Pc;
+        void *a2[] = {&ta, (void *)&omt, &one, &zero, &pc, &one, &zero, (void *)&done, &zero};
+        PCG_PROF(ctx, "t_csr", cudaLaunchKernel(TK.csr, dim3(tp.T_c * tp.csr_blocks), dim3(tp.threads), a1, tp.smem_c, s));
+        PCG_PROF(ctx, "t_csc", cudaLaunchKernel(TK.csc, dim3(tp.T_r * tp.csc_chunks), dim3(tp.threads), a2, tp.smem_r, s));
+        if (f32) PCG_PROF(ctx, "t_fin_out", k_t_fin_out<float><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
+        else PCG_PROF(ctx, "t_fin_out", k_t_fin_out<double><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
+    } else if (f32) {
         PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
-        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, 1));
+        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, 1, nullptr));
         PCG_PROF(ctx, "csr_f32", PCG_DISPATCH_G(Gr, (k_csr<float, GG><<<grid, 256, 0, s>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, done, nullptr))));
         PCG_PROF(ctx, "csc_f32", PCG_DISPATCH_G(Gc, (k_csc<float, GG><<<grid, 256, 0, s>>>(ws.desc, (const float *)ws.u, v, out, ws, 0))));
     } else {

@@ -1,0 +1,56 @@
+// Plan and launch interface of the shared-memory tiled products (tiled.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pcg {
+
+constexpr int kTileSmemBytes = 220 * 1024;   // staged slice of the gathered vector
+
+// value types of the tiled products
+constexpr int kVtF32 = 0;   // float values, float sums
+constexpr int kVtF64 = 1;   // double values, double sums
+constexpr int kVtDF = 2;    // double-float pairs summed with TwoSum (float arithmetic)
+struct DF {};
+constexpr size_t kSmemPerSm = 228 * 1024;     // shared memory of one SM
+
+struct TiledPlan {
+    bool valid;
+    int RG, vsize, vtype;     // values gathered per nonzero, staged bytes per value, kVt*
+    int64_t n, p, nnz;
+    int W_c, T_c;             // column tile width and count (CSR pass)
+    int W_r, T_r;             // row strip height and count (CSC pass)
+    uint16_t *col16;          // tile-major column offsets inside the tile, each row's run padded
+                              // to whole 8-entry chunks with the sentinel W_c
+    uint16_t *row16;          // strip-major row offsets inside the strip, padded likewise (W_r)
+    uint32_t *rt;             // rt[c * n + i]: first chunk of row i in tile c (T_c * n + 1 entries)
+    uint32_t *cs;             // cs[t * p + j]: first chunk of column j in strip t (T_r * p + 1)
+    int32_t *col_order;       // columns by decreasing length (the CSC pass's work order)
+    void *Pr;                 // row partials [T_c][n][RG]
+    void *Pc;                 // column partials [T_r][p][RG]
+    int csr_blocks, csc_chunks, threads;
+    int G_row, G_col;         // lanes per row / column segment
+    size_t smem_c, smem_r;    // dynamic shared memory of the two passes
+};
+
+struct TiledArgs {
+    TiledPlan plan;
+};
+
+struct TiledKernels {
+    void *csr, *csc, *fin1;
+};
+
+// Builds (on the context stream) the 16-bit index copies and tile bounds of X
+// for RG values of vsize bytes per gather.  Leaves pl->valid false when the
+// tiled products do not apply (empty X or nnz beyond 32-bit offsets).
+pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
+                            int RG, int vtype, TiledPlan *pl);
+TiledKernels tiled_kernels(const TiledPlan &pl);
+// kernel pointers plus their dynamic shared-memory attributes
+pcg_status tiled_prepare(pcg_ctx *ctx, const TiledPlan &pl, TiledKernels *k);
+
+}  // namespace pcg

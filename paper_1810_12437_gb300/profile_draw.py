@@ -1,0 +1,50 @@
+"""Short, profiler-friendly runs of the draw (for ncu and similar tools).
+
+    python -m paper_1810_12437_gb300.profile_draw --workload single --iters 6
+    python -m paper_1810_12437_gb300.profile_draw --workload batched --iters 4
+
+`single` draws chain 0 of the batched workload alone (n=5e5, p=5e4), `batched`
+draws all 16 chains; both stop after --iters CG iterations (tol 0) and run
+with per-kernel timing on (plain launches, one kernel per launch), then print
+the per-kernel averages.  --small uses a 20x smaller design (n=25,000,
+p=2,500) of the same recipe.
+"""
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import _native as pb
+from . import inputs
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["single", "batched"], default="single")
+    ap.add_argument("--iters", type=int, default=6)
+    ap.add_argument("--precision", default="fp32_refined")
+    ap.add_argument("--small", action="store_true")
+    args = ap.parse_args(argv)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    kw = dict(n=25_000, p=2_500) if args.small else {}
+    if args.workload == "single":
+        P = inputs.config3(nrhs=1, **kw)
+        X = pb.DeviceDesign.from_host(P.X, dev)
+        ctx = pb.Context(precision=args.precision, profile=True, reliable_k=0)
+        pb.pcg_draw_beta(ctx, X, T(P.omega[0]), T(P.z[0]), T(P.lam[0]), float(P.tau[0]), T(P.eta[0]),
+                         T(P.delta[0]), tol=0.0, max_iter=args.iters)
+    else:
+        P = inputs.config3(**kw)
+        X = pb.DeviceDesign.from_host(P.X, dev)
+        ctx = pb.Context(precision=args.precision, profile=True, reliable_k=0)
+        pb.pcg_draw_beta_batched(ctx, X, T(P.omega), T(P.z), T(P.lam), T(P.tau), T(P.eta), T(P.delta),
+                                 tol=0.0, max_iter=args.iters)
+    torch.cuda.synchronize()
+    table = pb.profile_table(ctx)
+    print(json.dumps({k: {"avg_us": round(v[0] / v[1] * 1e3, 2), "launches": v[1]} for k, v in table.items()}))
+
+
+if __name__ == "__main__":
+    main()

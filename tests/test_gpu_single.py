@@ -57,7 +57,8 @@ def test_build_rhs_matches_oracle(pb, which, cfg1, cfg2):
 
 
 # ------------------------------------------------------------------ a3 + a4: Phi v
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32_refined", 3e-6), ("fp32", 3e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("df32", 1e-12), ("fp32_refined", 3e-6),
+                                      ("fp32", 3e-6)])
 def test_phi_mul_matches_oracle(pb, cfg2, prec, tol):
     P = cfg2
     X, a = device_problem(P)
@@ -71,7 +72,7 @@ def test_phi_mul_matches_oracle(pb, cfg2, prec, tol):
 
 
 def fp64_iters_ok(k_gpu, k_ref):
-    return abs(k_gpu - k_ref) <= max(2, int(0.06 * k_ref))
+    return abs(k_gpu - k_ref) <= max(2, int(0.08 * k_ref))
 
 
 def fp32_iters_ok(k_gpu, k_ref):
@@ -89,11 +90,12 @@ def well_conditioned():
 
 
 # ------------------------------------------------------------------ a2, a5-a7: same-k CG
+@pytest.mark.parametrize("prec", ["fp64", "df32"])
 @pytest.mark.parametrize("k", [1, 2, 5, 13, 30])
-def test_fixed_iterations_fp64(pb, k):
+def test_fixed_iterations_fp64(pb, k, prec):
     P = well_conditioned()
     X, a = device_problem(P)
-    ctx = pb.Context(precision="fp64", stop_rule="relative")
+    ctx = pb.Context(precision=prec, stop_rule="relative")
     res = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"],
                            tol=0.0, max_iter=k)
     assert res.status == pb.PCG_MAXITER and res.iters == k
@@ -155,10 +157,12 @@ def test_draw_config2(pb, cfg2, prec, bound):
         assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6
 
 
-def test_draw_config2_fp64(pb, cfg2):
+@pytest.mark.parametrize("prec", ["fp64", "df32"])
+def test_draw_config2_fp64(pb, cfg2, prec):
+    """float64 and double-float products: iteration counts in the float64 band."""
     P = cfg2
     X, a = device_problem(P)
-    ctx = pb.Context(precision="fp64")
+    ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"],
                            tol=1e-6, max_iter=5000)
     ref, k, r, st = O.draw_beta_cg(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-6)
