@@ -6,8 +6,11 @@ Phi^-1) sharing one synthetic binary design X with n = 500,000 rows and
 p = 50,000 columns (column rates log10 r ~ U(-4.5, -1.5), about 1.15e8
 nonzeros), each chain with its own omega, lambda, tau, eta and delta;
 right-hand sides by Eq. 2.3 and prior-preconditioned CG to the paper's RMS
-rule 1e-6 (Eq. S2), float32 products with float64 scalars and float64
-reliable updates, one batched launch (CUDA graph) per step.
+rule 1e-6 (Eq. S2), one batched launch (CUDA graph) per step.  Products in
+double-float arithmetic (pairs of floats, about 48 bits: float64-like
+iteration counts at float32 instruction rates) with float64 CG scalars and
+vectors; PCG_BENCH_PRECISION=fp32_refined selects float32 products with
+float64 reliable updates instead.
 
 Printed (rank 0, one JSON line): beta-draws/s of the whole job, the
 end-to-end rate through the public API with host buffers, the roofline of the
@@ -39,7 +42,7 @@ METRIC = "beta-draws/sec and SpMV HBM GB/s vs peak at n=5e5,p=5e4; batched/adjoi
 UNIT = "beta-draws/s"
 NRHS = 16
 TOL = 1e-6
-PRECISION = os.environ.get("PCG_BENCH_PRECISION", "fp32_refined")
+PRECISION = os.environ.get("PCG_BENCH_PRECISION", "df32")
 RELIABLE_K = 50
 WORKLOAD = ("16 chains sharing binary X, n=500000, p=50000, log10 r_j~U(-4.5,-1.5), "
             "per-chain omega~U(.05,.25), half-Cauchy lambda (2% x100), log10 tau~U(-3.5,-2.5), "
@@ -194,6 +197,20 @@ def bytes_per_launch(kernel, n, p, nnz, RP, RG=1):
     return None
 
 
+def tuned_group_width(tune_file):
+    """RHS group width the library's autotuner chose (its cache file holds
+    lines `batch_rg:<n>:<p>:<nnz>:<RP>:<precision> <RG>`); 0 = untiled."""
+    rg = 1
+    try:
+        with open(tune_file) as fh:
+            for line in fh:
+                if line.startswith("batch_rg:"):
+                    rg = int(line.split()[1])
+    except (OSError, ValueError, IndexError):
+        pass
+    return rg
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("batched.cu", "tiled.cu", "tiled.h", "device_common.cuh", "internal.h"):
@@ -329,31 +346,40 @@ def run_ours(args):
     # roofline of the dominant kernel: per-kernel CUDA events on the launching stream
     pctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, profile=True,
                       autotune_cache=tune_file)
-    pb.pcg_draw_beta_batched(pctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
+    pres = pb.pcg_draw_beta_batched(pctx, X, **ins, tol=TOL, max_iter=20_000, out=out)
     table = pb.profile_table(pctx)
     RP = 16
-    # group width the autotuner chose: RP / RG tiled CSR launches per update launch
-    RG = 1
-    tiled_csr = "bt_csr_df32" if "bt_csr_df32" in table else "bt_csr_f32"
-    if tiled_csr in table and "b_update" in table:
-        # launches of one group's products per update launch (before compaction)
-        RG = max(1, round(RP * table["b_update"][1] / max(table[tiled_csr][1], 1)))
+    RG = tuned_group_width(tune_file)
+    # One tiled-product launch covers every RHS group still running (finished
+    # chains are compacted into the high slots and their groups exit at once):
+    # in iteration k that is ceil(live_k / RG) groups, live_k = chains with
+    # more than k iterations.
+    p_iters = list(pres.iters)
+    group_units = sum(-(-sum(1 for c in p_iters if c > k) // RG) for k in range(max(p_iters))) if RG else 0
+
+    def kernel_bytes(k, launches):
+        bb = bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP, RG)
+        if bb is None:
+            return None
+        return bb * (group_units if k.startswith("bt_cs") else launches)
+
     top = max(table.items(), key=lambda kv: kv[1][0])
     kname, (kms, kn) = top
     avg_s = kms / kn / 1e3
-    bpl = bytes_per_launch(kname, P.X.n, P.X.p, P.X.nnz, RP, RG)
+    tb = kernel_bytes(kname, kn)
+    bpl = tb / kn if tb else None
     peak, peak_kind = peaks()
     achieved = bpl / avg_s / 1e9 if bpl else None
     total_ms = sum(v[0] for v in table.values())
     per_k = {}
     for k, v in sorted(table.items()):
-        bb = bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP, RG)
+        bb = kernel_bytes(k, v[1])
         per_k[k] = {"avg_us": round(v[0] / v[1] * 1e3, 2), "launches": v[1],
-                    "GBps": round(bb / (v[0] / v[1] / 1e3) / 1e9, 1) if bb else None}
+                    "GBps": round(bb / (v[0] / 1e3) / 1e9, 1) if bb else None}
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic_for(kname),
             "peak_source": f"hbm_gbs of {peak_kind}", "avg_launch_us": avg_s * 1e6,
-            "algorithmic_bytes_per_launch": bpl, "rhs_group": RG,
+            "algorithmic_bytes_per_launch": bpl, "rhs_group": RG, "group_products": group_units,
             "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in sorted(table.items())},
             "per_kernel": per_k}
 
@@ -368,7 +394,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32x2" if PRECISION == "df32" else ("f64" if PRECISION == "fp64" else "f32"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": P.X.n, "p": P.X.p, "nnz": P.X.nnz, "nrhs": NRHS,
                    "tol": TOL, "precision": PRECISION,
                    "parallelism": f"replicas x{world} (independent chains per GPU)",

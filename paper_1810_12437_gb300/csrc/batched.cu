@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "df.cuh"
 #include "internal.h"
 #include "tiled.h"
 
@@ -34,6 +35,7 @@ struct BatchDesc {
     double tol;
     int max_iter, stop_rule, refined, reliable_k;
     int RG;   // right-hand sides per tiled product group (0: untiled products)
+    int df;   // double-float products: s32 / om32 hold float pairs (float2)
 };
 
 // flags[] layout (kFlagInts ints, device):
@@ -46,10 +48,10 @@ constexpr int kFlagInts = 128;
 
 struct BatchWs {
     double *b, *r, *s64, *v64, *beta, *m, *dg;   // p*RP each (interleaved)
-    float *s32;                                  // p*RP
+    float *s32;                                  // p*RP floats, or p*RP float pairs (df)
     void *u;                                     // n*RP doubles (w64, then u32 / u64)
     double *om64;                                // n*RP
-    float *om32;                                 // n*RP
+    float *om32;                                 // n*RP floats, or n*RP float pairs (df)
     double *partials;                            // kMaxReduceBlocks * 32
     unsigned int *counters;                      // 16
     CgScalars *sc;                               // 32
@@ -175,7 +177,8 @@ __global__ void k_b_prep(const BatchDesc *__restrict__ d, double *__restrict__ w
         }
         w[i * RP + r] = wv;
         om64[i * RP + r] = o;
-        om32[i * RP + r] = (float)o;
+        if (d->df) reinterpret_cast<float2 *>(om32)[i * RP + r] = df_from_double(o);
+        else om32[i * RP + r] = (float)o;
     }
 }
 
@@ -214,7 +217,8 @@ __global__ void __launch_bounds__(256) k_b_init(const BatchDesc *__restrict__ d,
                 ws.m[o] = m;
                 ws.dg[o] = dg;
                 ws.s64[o] = zz;
-                ws.s32[o] = (float)zz;
+                if (d->df) reinterpret_cast<float2 *>(ws.s32)[o] = df_from_double(zz);
+                else ws.s32[o] = (float)zz;
                 ws.beta[o] = 0.0;
                 rho[q] += b * zz;
             }
@@ -388,9 +392,9 @@ __global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         PT acc = Pc[t];
-        for (int k = 1; k < T_r; ++k) acc += Pc[(size_t)k * total + t];
+        for (int k = 1; k < T_r; ++k) acc = part_add(acc, Pc[(size_t)k * total + t]);
         const double s = ws.s64[t];
-        const double v = (double)acc + ws.dg[t] * s;
+        const double v = part_to_double(acc) + ws.dg[t] * s;
         ws.v64[t] = v;
         sg += s * v;
     }
@@ -609,11 +613,13 @@ __global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d,
     if (r >= d->R || ws.sc[r].done) return;
     const double gamma = ws.sc[r].gamma;
     const int64_t total = d->p * RP;
+    const bool df = d->df != 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double s = ws.m[t] * ws.r[t] + gamma * ws.s64[t];
         ws.s64[t] = s;
-        ws.s32[t] = (float)s;
+        if (df) reinterpret_cast<float2 *>(ws.s32)[t] = df_from_double(s);
+        else ws.s32[t] = (float)s;
     }
 }
 
@@ -687,12 +693,14 @@ __global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__rest
         permute_row<RP>(ws.beta + o, perm);
         permute_row<RP>(ws.m + o, perm);
         permute_row<RP>(ws.dg + o, perm);
-        permute_row<RP>(ws.s32 + o, perm);
+        if (d->df) permute_row<RP>(reinterpret_cast<float2 *>(ws.s32) + o, perm);
+        else permute_row<RP>(ws.s32 + o, perm);
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const size_t o = (size_t)i * RP;
-        permute_row<RP>(ws.om32 + o, perm);
+        if (d->df) permute_row<RP>(reinterpret_cast<float2 *>(ws.om32) + o, perm);
+        else permute_row<RP>(ws.om32 + o, perm);
         permute_row<RP>(ws.om64 + o, perm);
     }
 }
@@ -716,11 +724,11 @@ __global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restric
 // ===========================================================================
 
 static cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps,
-                            size_t ndeps, void *func, int grid, int block, void **args,
+                            size_t ndeps, void *func, dim3 grid, int block, void **args,
                             size_t smem = 0) {
     cudaKernelNodeParams kp = {};
     kp.func = func;
-    kp.gridDim = dim3(grid);
+    kp.gridDim = grid;
     kp.blockDim = dim3(block);
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
@@ -735,7 +743,7 @@ template <int RP>
 static BatchKernels batch_kernels(bool df) {
     return {(void *)k_b_init<RP>,         (void *)k_b_csr<RP>,          (void *)k_b_csr64<RP>,
             (void *)k_b_csc<RP>,
-            df ? (void *)k_b_fin<RP, double> : (void *)k_b_fin<RP, float>,
+            df ? (void *)k_b_fin<RP, float2> : (void *)k_b_fin<RP, float>,
             (void *)k_b_update<RP>,
             (void *)k_b_true_resid<RP>,   (void *)k_b_sdir<RP>,         (void *)k_b_compact_plan<RP>,
             (void *)k_b_compact_apply<RP>};
@@ -778,8 +786,7 @@ struct BatchNodeArgs {
     TiledArgs ta;
     void *pc_all;
     const void *s_src, *om_src;
-    int goff[kMaxBatch];
-    const int *ggate[kMaxBatch];   // per product group: skip when flags[96 + g] != 0
+    const int *gate_base;          // product group g is skipped when gate_base[g] != 0
 };
 
 // Adds the products of one iteration to `body` after `dep`; returns the last node.
@@ -796,20 +803,15 @@ static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, in
         return add_node(body, last, &n1, 1, K.csc, grid, 256, a2);
     }
     const TiledPlan &P = bp.plan;
-    cudaGraphNode_t prev = dep ? *dep : nullptr;
-    int nprev = dep ? ndep : 0;
-    for (int g = 0; g < RP / bp.RG; ++g) {
-        cudaGraphNode_t nc, nr;
-        void *a1[] = {&A.ta, &A.s_src, &A.RPv, &A.goff[g], &A.ggate[g], &A.zero};
-        e = add_node(body, &nc, nprev ? &prev : nullptr, nprev, bp.tk.csr, P.T_c * P.csr_blocks, P.threads,
-                     a1, P.smem_c);
-        if (e != cudaSuccess) return e;
-        void *a2[] = {&A.ta, &A.om_src, &A.RPv, &A.goff[g], &A.pc_all, &A.RPv, &A.goff[g], &A.ggate[g], &A.zero};
-        e = add_node(body, &nr, &nc, 1, bp.tk.csc, P.T_r * P.csc_chunks, P.threads, a2, P.smem_r);
-        if (e != cudaSuccess) return e;
-        prev = nr;
-        nprev = 1;
-    }
+    // every RHS group in one launch (blockIdx.y); finished groups exit at once
+    cudaGraphNode_t nc, prev;
+    void *a1[] = {&A.ta, &A.s_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+    e = add_node(body, &nc, dep, dep ? ndep : 0, bp.tk.csr, dim3(P.T_c * P.csr_blocks, RP / bp.RG), P.threads, a1,
+                 P.smem_c);
+    if (e != cudaSuccess) return e;
+    void *a2[] = {&A.ta, &A.om_src, &A.RPv, &A.zero, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+    e = add_node(body, &prev, &nc, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2, P.smem_r);
+    if (e != cudaSuccess) return e;
     void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.ws};
     return add_node(body, last, &prev, 1, K.fin, gvec, 256, a3);
 }
@@ -838,13 +840,10 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
     A.RPv = RP;
     A.ta.plan = bp.plan;
     A.pc_all = bp.pc_all;
-    A.s_src = bp.df ? (const void *)ws.s64 : (const void *)ws.s32;
-    A.om_src = bp.df ? (const void *)ws.om64 : (const void *)ws.om32;
+    A.s_src = ws.s32;    // float32 values, or float pairs in the double-float mode
+    A.om_src = ws.om32;
     A.T_r = bp.plan.T_r;
-    for (int g = 0; g < kMaxBatch; ++g) {
-        A.goff[g] = g * (bp.RG > 0 ? bp.RG : 1);
-        A.ggate[g] = ws.flags + 96 + g;
-    }
+    A.gate_base = ws.flags + 96;
     cudaGraph_t g = nullptr;
     PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
     cudaError_t e;
@@ -930,22 +929,20 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
         const TiledPlan &P = bp.plan;
         TiledArgs ta{P};
         int rp = RP, zero = 0, T_r = P.T_r;
-        const void *s32 = bp.df ? (const void *)ws.s64 : (const void *)ws.s32;
-        const void *om32 = bp.df ? (const void *)ws.om64 : (const void *)ws.om32;
+        const void *s32 = ws.s32;    // float32 values, or float pairs in the double-float mode
+        const void *om32 = ws.om32;
         void *pc = bp.pc_all;
         const int *flags = ws.flags;
         const BatchDesc *dd = ws.desc;
         BatchWs wsv = ws;
-        for (int g = 0; g < RP / bp.RG; ++g) {
-            int off = g * bp.RG;
-            const int *gate = flags + 96 + g;
-            void *a1[] = {&ta, (void *)&s32, &rp, &off, (void *)&gate, &zero};
-            void *a2[] = {&ta, (void *)&om32, &rp, &off, &pc, &rp, &off, (void *)&gate, &zero};
-            PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, dim3(P.T_c * P.csr_blocks), dim3(P.threads), a1, P.smem_c, st));
-            PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, dim3(P.T_r * P.csc_chunks), dim3(P.threads), a2, P.smem_r, st));
-        }
+        const int *gate = flags + 96;
+        void *a1[] = {&ta, (void *)&s32, &rp, &zero, (void *)&gate, &zero};
+        void *a2[] = {&ta, (void *)&om32, &rp, &zero, &pc, &rp, &zero, (void *)&gate, &zero};
+        const dim3 gc(P.T_c * P.csr_blocks, RP / bp.RG), gr(P.T_r * P.csc_chunks, RP / bp.RG);
+        PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, gc, dim3(P.threads), a1, P.smem_c, st));
+        PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, gr, dim3(P.threads), a2, P.smem_r, st));
         void *a3[] = {(void *)&dd, &pc, &T_r, &wsv};
-        PCG_PROF(ctx, "bt_fin", cudaLaunchKernel(bp.df ? (void *)k_b_fin<RP, double> : (void *)k_b_fin<RP, float>,
+        PCG_PROF(ctx, "bt_fin", cudaLaunchKernel(bp.df ? (void *)k_b_fin<RP, float2> : (void *)k_b_fin<RP, float>,
                                                  dim3(gvec), dim3(256), a3, 0, st));
     }
     PCG_PROF(ctx, "b_update", k_b_update<RP><<<gvec, 256, 0, st>>>(ws.desc, ws, 0, 0));
@@ -975,7 +972,7 @@ static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *
     if (RG == 0) RG = 1;   // double-float products exist only in tiled form
     char tag[32];
     snprintf(tag, sizeof tag, "batch%d%s", RG, df ? "d" : "");
-    pcg_status st = build_tiled_plan(ctx, tag, Xr, Xc, RG, df ? kVtDF : kVtF32, &bp->plan);
+    pcg_status st = build_tiled_plan(ctx, tag, Xr, Xc, RG, df ? kVtDF : kVtF32, RP / RG, true, &bp->plan);
     if (st != PCG_OK) return st;
     if (!bp->plan.valid) return PCG_OK;
     st = tiled_prepare(ctx, bp->plan, &bp->tk);
@@ -998,7 +995,7 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
         snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p|%d%s:%d:%d:%d:%d:%d:%d:%lld:%lld:%p:%p:%p:%p:%p:%p",
                  RP, (int)refined, grid, gvec, (void *)ws.b, ws.u, (void *)ws.om64, (void *)ws.om32, bp.RG, bp.df ? "d" : "",
                  bp.plan.T_c, bp.plan.T_r, bp.plan.csr_blocks, bp.plan.csc_chunks,
-                 bp.plan.G_row * 64 + bp.plan.G_col, bp.plan.threads, (long long)bp.plan.n,
+                 bp.plan.nw, bp.plan.threads, (long long)bp.plan.n,
                  (long long)bp.plan.p, (void *)bp.plan.col16, (void *)bp.plan.row16, (void *)bp.plan.rt,
                  (void *)bp.plan.cs, bp.plan.Pr, (void *)bp.pc_all);
         auto it = ctx->named_graphs.find(key);
@@ -1019,7 +1016,7 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
         // float64 recomputation of r
         int trips = 1;
         for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
-        const int per_trip = (bp.RG ? 2 * (RP / bp.RG) + 1 + 2 : 2) + 2;
+        const int per_trip = (bp.RG ? 2 + 1 + 2 : 2) + 2;
         ctx->last_launches += 3 + (int64_t)per_trip * trips + 2 * (int64_t)hflags[2];
         return PCG_OK;
     }
@@ -1070,8 +1067,8 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
         return PCG_OK;
     }
     char key[128];
-    snprintf(key, sizeof key, "batch_rg:%lld:%lld:%lld:%d", (long long)Xr->n, (long long)Xr->p,
-             (long long)Xr->nnz, RP);
+    snprintf(key, sizeof key, "batch_rg:%lld:%lld:%lld:%d:%d", (long long)Xr->n, (long long)Xr->p,
+             (long long)Xr->nnz, RP, ctx->opt.precision);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end() && !it->second.empty()) {
         *rg_out = it->second[0];
@@ -1162,7 +1159,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
     // one block for the p-sized vectors and the small state
-    const size_t total_p = 7 * up(vp) + up(sizeof(float) * (size_t)p * RP) +
+    const size_t total_p = 7 * up(vp) + up(sizeof(float2) * (size_t)p * RP) +
                            up(sizeof(double) * kMaxReduceBlocks * 32) + up(64 * sizeof(unsigned)) +
                            up(sizeof(CgScalars) * kMaxBatch) + up(sizeof(int) * kFlagInts) + up(sizeof(BatchDesc));
     cudaError_t e;
@@ -1172,7 +1169,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     if (!bu) return cuda_error(ctx, e, "allocating the batched workspace");
     double *bom64 = (double *)grow(ctx, "batch_om64", sizeof(double) * (size_t)n * RP, &e);
     if (!bom64) return cuda_error(ctx, e, "allocating the batched workspace");
-    float *bom32 = (float *)grow(ctx, "batch_om32", sizeof(float) * (size_t)n * RP, &e);
+    float *bom32 = (float *)grow(ctx, "batch_om32", sizeof(float2) * (size_t)n * RP, &e);
     if (!bom32) return cuda_error(ctx, e, "allocating the batched workspace");
     BatchWs ws{};
     size_t off = 0;
@@ -1184,7 +1181,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     ws.beta = (double *)take(vp);
     ws.m = (double *)take(vp);
     ws.dg = (double *)take(vp);
-    ws.s32 = (float *)take(sizeof(float) * (size_t)p * RP);
+    ws.s32 = (float *)take(sizeof(float2) * (size_t)p * RP);
     ws.partials = (double *)take(sizeof(double) * kMaxReduceBlocks * 32);
     ws.counters = (unsigned *)take(64 * sizeof(unsigned));
     ws.sc = (CgScalars *)take(sizeof(CgScalars) * kMaxBatch);
@@ -1222,6 +1219,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     d.stop_rule = ctx->opt.stop_rule;
     d.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
+    d.df = ctx->opt.precision == PCG_PREC_DF32 ? 1 : 0;
     const bool refined = d.refined != 0;
     int RG = 0;
     pcg_status st = choose_rg(ctx, Xr, Xc, ws, d, hd, RP, refined, nrhs, hsc, hflags, &RG);

@@ -52,15 +52,18 @@ struct DrawDesc {
     int64_t n, p, nnz;
     double tau, tol;
     int max_iter, stop_rule, refined, reliable_k;
+    int df;                // double-float products: keep s (and omega) as float pairs too
 };
 
 // Device workspace of the single-RHS path (sizes grow on demand).
 struct SingleWs {
     double *b, *r, *s64, *v64;    // p each
     float *s32;                   // p
+    float2 *sdf;                  // p (s as double-float pairs, DF32 mode)
     void *u;                      // n doubles (aliased as n floats in FP32 modes)
     float *om32;                  // n
     double *om64;                 // n (float64 omega for the tiled float64 products)
+    float2 *omdf;                 // n (omega as double-float pairs, DF32 mode)
     double *partials;             // kMaxReduceBlocks * 4
     unsigned int *counters;       // 16
     CgScalars *sc;                // 1
@@ -120,6 +123,8 @@ struct pcg_ctx {
     int64_t last_launches = 0;
     // shared-memory tiled products (on unless PCG_BETA_TILED=0 in the environment)
     bool tiled_enabled = true;
+    // bank-aware entry order in the tiled plan (on unless PCG_BETA_BANK_PERMUTE=0)
+    bool bank_permute = true;
 };
 
 namespace pcg {

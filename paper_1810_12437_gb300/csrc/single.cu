@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "df.cuh"
 #include "internal.h"
 #include "tiled.h"
 
@@ -54,7 +55,7 @@ __device__ __forceinline__ bool gate_closed(const int *done, const int *need) {
 // ---------------------------------------------------------------------------
 __global__ void k_rhs_w(const DrawDesc *__restrict__ d, double *__restrict__ w,
                         float *__restrict__ om32, int want_w, int want_om32,
-                        double *__restrict__ om64) {
+                        double *__restrict__ om64, float2 *__restrict__ omdf) {
     const int64_t n = d->n;
     const double *__restrict__ om = d->omega;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -63,6 +64,7 @@ __global__ void k_rhs_w(const DrawDesc *__restrict__ d, double *__restrict__ w,
         if (want_w) w[i] = o * d->z[i] + sqrt(o) * d->eta[i];
         if (want_om32) om32[i] = (float)o;
         if (om64) om64[i] = o;
+        if (omdf) omdf[i] = df_from_double(o);
     }
 }
 
@@ -76,8 +78,8 @@ __global__ void k_t_fin_out(const DrawDesc *__restrict__ d, TiledArgs A, const d
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         T acc = Pc[j];
-        for (int t = 1; t < P.T_r; ++t) acc += Pc[(size_t)t * p + j];
-        out[j] = (double)acc + prior_prec(d->tau, d->lambda[j]) * v[j];
+        for (int t = 1; t < P.T_r; ++t) acc = part_add(acc, Pc[(size_t)t * p + j]);
+        out[j] = part_to_double(acc) + prior_prec(d->tau, d->lambda[j]) * v[j];
     }
 }
 
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
             ws.r[j] = b;
             ws.s64[j] = z;
             ws.s32[j] = (float)z;
+            if (d->df) ws.sdf[j] = df_from_double(z);
             d->beta[j] = 0.0;
             rho += b * z;
         }
@@ -370,7 +373,15 @@ __global__ void __launch_bounds__(256) k_sdir(const DrawDesc *__restrict__ d, Si
         const double s = prior_var(tau, d->lambda[j]) * ws.r[j] + gamma * ws.s64[j];
         ws.s64[j] = s;
         ws.s32[j] = (float)s;
+        if (d->df) ws.sdf[j] = df_from_double(s);
     }
+}
+
+// v (float64) -> double-float pairs (pcg_phi_mul in the DF32 mode)
+__global__ void k_to_df(const double *__restrict__ x, float2 *__restrict__ y, int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        y[j] = df_from_double(x[j]);
 }
 
 // v (float64) -> float32 copy (pcg_phi_mul in the float32 modes)
@@ -472,7 +483,7 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     const size_t szp64 = up(sizeof(double) * cp), szp32 = up(sizeof(float) * cp);
     const size_t szn32 = up(sizeof(float) * cn), szn64 = up(sizeof(double) * cn);
     const size_t szpart = up(sizeof(double) * kMaxReduceBlocks * 4);
-    const size_t total = 4 * szp64 + szp32 + szn32 + szn64 + szpart + up(64 * sizeof(unsigned)) +
+    const size_t total = 5 * szp64 + szp32 + szn32 + 2 * szn64 + szpart + up(64 * sizeof(unsigned)) +
                          up(sizeof(CgScalars)) + up(sizeof(DrawDesc));
     char *base = nullptr;
     PCG_CUDA_TRY(ctx, cudaMalloc(&base, total));
@@ -485,8 +496,10 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     w.s64 = (double *)take(szp64);
     w.v64 = (double *)take(szp64);
     w.s32 = (float *)take(szp32);
+    w.sdf = (float2 *)take(szp64);
     w.om32 = (float *)take(szn32);
     w.om64 = (double *)take(szn64);
+    w.omdf = (float2 *)take(szn64);
     w.partials = (double *)take(szpart);
     w.counters = (unsigned *)take(up(64 * sizeof(unsigned)));
     w.sc = (CgScalars *)take(up(sizeof(CgScalars)));
@@ -546,7 +559,8 @@ struct NodeArgs {
     int one, zero, want_w, want_om32, use_cond_ru;
     TiledArgs ta;
     double *om64;
-    const void *om_t;
+    float2 *omdf;
+    const void *om_t, *s_t;
     void *pc;
 };
 
@@ -573,6 +587,7 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
     A.om32 = ctx->ws.om32;
     A.want_w = d.rhs == nullptr ? 1 : 0;
     A.want_om32 = f32 ? 1 : 0;
+    const bool df = precision == PCG_PREC_DF32;
     A.s_gather = f32 ? (const void *)ctx->ws.s32 : (const void *)ctx->ws.s64;
     A.om = f32 ? (const void *)ctx->ws.om32 : nullptr;   // NULL: float64 omega from the descriptor
     A.u = ctx->ws.u;
@@ -583,8 +598,11 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
     A.zero = 0;
     A.use_cond_ru = refined ? 1 : 0;
     A.ta.plan = tp;
-    A.om64 = (tiled && !f32) ? ctx->ws.om64 : nullptr;
-    A.om_t = f32 ? (const void *)ctx->ws.om32 : (const void *)ctx->ws.om64;
+    A.om64 = (tiled && !f32 && !df) ? ctx->ws.om64 : nullptr;
+    A.omdf = (tiled && df) ? ctx->ws.omdf : nullptr;
+    // sources of the tiled products: float32, double-float pairs or float64
+    A.om_t = f32 ? (const void *)ctx->ws.om32 : df ? (const void *)ctx->ws.omdf : (const void *)ctx->ws.om64;
+    A.s_t = f32 ? (const void *)ctx->ws.s32 : df ? (const void *)ctx->ws.sdf : (const void *)ctx->ws.s64;
     A.pc = tp.Pc;
 
     cudaGraph_t g = nullptr;
@@ -593,7 +611,7 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
     cudaGraphNode_t n_w, n_init, n_while, n_csr, n_csc, n_upd, n_if, n_sdir, n_rcsr, n_tr;
     cudaGraph_t body = nullptr;
     {
-        void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32, &A.om64};
+        void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32, &A.om64, &A.omdf};
         e = add_kernel(g, &n_w, nullptr, 0, (void *)k_rhs_w, L.grid_stream, L.threads, args);
     }
     if (e == cudaSuccess) {
@@ -614,7 +632,7 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
     if (e == cudaSuccess && tiled) {
         // tiled products: CSR tiles -> CSC strips -> finalize (sigma, alpha)
         cudaGraphNode_t n_tc;
-        void *a1[] = {&A.ta, &A.s_gather, &A.one, &A.zero, &A.done, &A.zero};
+        void *a1[] = {&A.ta, &A.s_t, &A.one, &A.zero, &A.done, &A.zero};
         e = add_kernel(body, &n_csr, nullptr, 0, TK.csr, tp.T_c * tp.csr_blocks, tp.threads, a1, tp.smem_c);
         if (e == cudaSuccess) {
             void *a2[] = {&A.ta, &A.om_t, &A.one, &A.zero, &A.pc, &A.one, &A.zero, &A.done, &A.zero};
@@ -696,15 +714,17 @@ static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, cons
     const DrawDesc *dd = ws.desc;
     cudaStream_t st = ctx->stream;
     const int B = L.threads;
+    const bool df = precision == PCG_PREC_DF32;
     PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32,
-                                                                (tp.valid && !f32) ? ws.om64 : nullptr));
+                                                                (tp.valid && !f32 && !df) ? ws.om64 : nullptr,
+                                                                (tp.valid && df) ? ws.omdf : nullptr));
     PCG_PROF(ctx, "rhs_init", PCG_DISPATCH_G(L.G_col, (k_rhs_init<GG><<<L.grid_stream, B, 0, st>>>(dd, (const double *)ws.u, ws))));
     const int *done = &ws.sc->done, *need = &ws.sc->need_ru;
     for (int it = 0;; it += 8) {
         for (int k = 0; k < 8; ++k) {
             if (tp.valid) {
-                const void *sg = f32 ? (const void *)ws.s32 : (const void *)ws.s64;
-                const void *omt = f32 ? (const void *)ws.om32 : (const void *)ws.om64;
+                const void *sg = f32 ? (const void *)ws.s32 : df ? (const void *)ws.sdf : (const void *)ws.s64;
+                const void *omt = f32 ? (const void *)ws.om32 : df ? (const void *)ws.omdf : (const void *)ws.om64;
                 int one = 1, zero = 0;
                 void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
                 void *pc = tp.Pc;
@@ -752,6 +772,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     DrawDesc d = din;
     d.refined = (precision == PCG_PREC_FP32_REFINED) ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
+    d.df = precision == PCG_PREC_DF32 ? 1 : 0;
     *ctx->h_desc = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
                                       cudaMemcpyHostToDevice, ctx->stream));
@@ -760,7 +781,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         const pcg_csr xr{d.n, d.p, d.nnz, d.row_ptr, d.col_idx};
         const pcg_csc xc{d.n, d.p, d.nnz, d.col_ptr, d.row_idx};
         const int vt = precision == PCG_PREC_FP64 ? kVtF64 : precision == PCG_PREC_DF32 ? kVtDF : kVtF32;
-        st = build_tiled_plan(ctx, "single", &xr, &xc, 1, vt, &tp);
+        st = build_tiled_plan(ctx, "single", &xr, &xc, 1, vt, 1, true, &tp);
         if (st != PCG_OK) return st;
     }
     if (ctx->opt.use_graph && !ctx->opt.profile) {
@@ -770,7 +791,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         char key[256];
         snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d|%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p",
                  L.G_row, L.G_col, L.grid_stream, L.grid_vec, precision, d.refined, mode, (int)tp.valid,
-                 tp.W_c, tp.T_c, tp.W_r, tp.T_r, tp.csr_blocks, tp.csc_chunks, tp.G_row * 64 + tp.G_col,
+                 tp.W_c, tp.T_c, tp.W_r, tp.T_r, tp.csr_blocks, tp.csc_chunks, tp.nw,
                  (void *)tp.col16, (void *)tp.row16, (void *)tp.rt, (void *)tp.cs, tp.Pr, tp.Pc);
         // n and p enter through the plan only when it is valid
         std::string skey = std::string(key) + (tp.valid ? ":" + std::to_string(tp.n) + ":" + std::to_string(tp.p) : "");
@@ -830,7 +851,7 @@ pcg_status launch_build_rhs(pcg_ctx *ctx, const pcg_csc *X, const double *omega,
                                       cudaMemcpyHostToDevice, ctx->stream));
     const int grid = std::min(ctx->num_sms * 8, kMaxReduceBlocks);
     const int G = pick_group(d.p > 0 ? (double)d.nnz / d.p : 1.0);
-    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (double *)ctx->ws.u, ctx->ws.om32, 1, 0, nullptr));
+    PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (double *)ctx->ws.u, ctx->ws.om32, 1, 0, nullptr, nullptr));
     PCG_PROF(ctx, "rhs_b", PCG_DISPATCH_G(G, (k_rhs_b<GG><<<grid, 256, 0, ctx->stream>>>(ctx->ws.desc, (const double *)ctx->ws.u, b))));
     PCG_CUDA_TRY(ctx, cudaGetLastError());
     PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -869,7 +890,7 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
     TiledPlan tp{};
     if (ctx->tiled_enabled) {
         const int vt = prec == PCG_PREC_FP64 ? kVtF64 : prec == PCG_PREC_DF32 ? kVtDF : kVtF32;
-        pcg_status st2 = build_tiled_plan(ctx, "single", Xr, Xc, 1, vt, &tp);
+        pcg_status st2 = build_tiled_plan(ctx, "single", Xr, Xc, 1, vt, 1, false, &tp);
         if (st2 != PCG_OK) return st2;
     }
     if (tp.valid) {
@@ -877,11 +898,14 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
         pcg_status st2 = tiled_prepare(ctx, tp, &TK);
         if (st2 != PCG_OK) return st2;
         TiledArgs ta{tp};
+        const bool df = prec == PCG_PREC_DF32;
         if (f32) PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
+        if (df) PCG_PROF(ctx, "to_df", k_to_df<<<grid, 256, 0, s>>>(v, ws.sdf, d.p));
         PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, f32 ? 1 : 0,
-                                                            f32 ? nullptr : ws.om64));
-        const void *sg = f32 ? (const void *)ws.s32 : (const void *)v;
-        const void *omt = f32 ? (const void *)ws.om32 : (const void *)ws.om64;
+                                                            (f32 || df) ? nullptr : ws.om64,
+                                                            df ? ws.omdf : nullptr));
+        const void *sg = f32 ? (const void *)ws.s32 : df ? (const void *)ws.sdf : (const void *)v;
+        const void *omt = f32 ? (const void *)ws.om32 : df ? (const void *)ws.omdf : (const void *)ws.om64;
         int one = 1, zero = 0;
         void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
         void *pc = tp.Pc;
@@ -889,10 +913,11 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
         PCG_PROF(ctx, "t_csr", cudaLaunchKernel(TK.csr, dim3(tp.T_c * tp.csr_blocks), dim3(tp.threads), a1, tp.smem_c, s));
         PCG_PROF(ctx, "t_csc", cudaLaunchKernel(TK.csc, dim3(tp.T_r * tp.csc_chunks), dim3(tp.threads), a2, tp.smem_r, s));
         if (f32) PCG_PROF(ctx, "t_fin_out", k_t_fin_out<float><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
+        else if (df) PCG_PROF(ctx, "t_fin_out", k_t_fin_out<float2><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
         else PCG_PROF(ctx, "t_fin_out", k_t_fin_out<double><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
     } else if (f32) {
         PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
-        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, 1, nullptr));
+        PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, 1, nullptr, nullptr));
         PCG_PROF(ctx, "csr_f32", PCG_DISPATCH_G(Gr, (k_csr<float, GG><<<grid, 256, 0, s>>>(ws.desc, ws.s32, ws.om32, (float *)ws.u, done, nullptr))));
         PCG_PROF(ctx, "csc_f32", PCG_DISPATCH_G(Gc, (k_csc<float, GG><<<grid, 256, 0, s>>>(ws.desc, (const float *)ws.u, v, out, ws, 0))));
     } else {

@@ -30,6 +30,7 @@
 #include <cub/cub.cuh>
 
 #include "device_common.cuh"
+#include "df.cuh"
 #include "internal.h"
 #include "tiled.h"
 
@@ -40,12 +41,15 @@ namespace pcg {
 // ---------------------------------------------------------------------------
 
 // bounds[t * nseg + s] = first position in segment s whose index is >= t * W,
-// for t = 0..T (t = 0 gives the segment start, t = T its end).
+// for t = 0..T (t = 0 gives the segment start, t = T its end).  Segment s is
+// the stored segment order[s] when an order is given.
 __global__ void k_plan_bounds(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                              int64_t nseg, int W, int T, uint32_t *__restrict__ bounds) {
+                              const int32_t *__restrict__ order, int64_t nseg, int W, int T,
+                              uint32_t *__restrict__ bounds) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = ptr[s], b = ptr[s + 1];
+        const int64_t o = order ? (int64_t)order[s] : s;
+        const int64_t a = ptr[o], b = ptr[o + 1];
         bounds[s] = (uint32_t)a;
         int64_t lo = a;
         for (int t = 1; t < T; ++t) {
@@ -101,6 +105,177 @@ __global__ void k_plan_fill(const int32_t *__restrict__ idx, const uint32_t *__r
     }
 }
 
+// The sentinel chunk: 8 copies of W (every entry reads the zero slot), read by
+// lanes whose segment has no chunk left.
+__global__ void k_plan_sentinel(uint16_t *__restrict__ chunk, int W) {
+    if (threadIdx.x < 8) chunk[threadIdx.x] = (uint16_t)W;
+}
+
+// Work split: split[t * (nwt + 1) + k] = first segment of the k-th of nwt
+// warps in tile t, chosen so that the warps get equal costs, a segment's cost
+// being its chunks plus kSegCost (its bounds, reduction and output)
+// (split[.. + 0] = 0 and split[.. + nwt] = nseg, so every segment, empty ones
+// included, belongs to exactly one warp).
+__global__ void k_plan_split(const uint32_t *__restrict__ cb, int64_t nseg, int T, int nwt,
+                             int32_t *__restrict__ split) {
+    const int64_t total = (int64_t)T * (nwt + 1);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = q / (nwt + 1);
+        const int k = (int)(q - t * (nwt + 1));
+        int64_t s;
+        if (k == 0) {
+            s = 0;
+        } else if (k == nwt) {
+            s = nseg;
+        } else {
+            const uint64_t c0 = cb[t * nseg];
+            const uint64_t total = (uint64_t)cb[(t + 1) * nseg] - c0 + (uint64_t)kSegCost * (uint64_t)nseg;
+            const uint64_t target = total * (uint64_t)k / (uint64_t)nwt;
+            int64_t l = 0, h = nseg;   // first segment whose cost prefix reaches the target
+            while (l < h) {
+                const int64_t m = (l + h) >> 1;
+                if ((uint64_t)cb[t * nseg + m] - c0 + (uint64_t)kSegCost * (uint64_t)m < target) l = m + 1;
+                else h = m;
+            }
+            s = l;
+        }
+        split[q] = (int32_t)s;
+    }
+}
+
+// lanes per segment (log2) for a warp whose segments hold `chunks` chunks in all
+__device__ __forceinline__ int lanes_log2(uint32_t chunks, uint32_t nseg) {
+    const uint32_t mean = (chunks + nseg - 1) / nseg;
+    int lg = 1;
+    while (lg < 5 && ((uint32_t)kBlk << lg) < mean) ++lg;
+    return lg;
+}
+
+// Bank-aware entry order.  In the products (warp_segments) each lane walks
+// every G-th chunk of its segment in blocks of kBlk, and the k-th shared-memory
+// load of a block (chunk k / 8 of the lane's block, entry k % 8) is one
+// instruction over the warp whose cost is the largest number of distinct words
+// any bank serves.  Entries of one segment can be placed in any of its load
+// slots without changing the sum.  This kernel replays the products' schedule
+// (the same work split, lanes per segment, rounds and blocks) and, slot by
+// slot, lets the lanes of each bank phase claim entries of their block in
+// distinct banks: kPermRounds rounds of proposals (each lane proposes a bank
+// it still holds, rotated per lane and slot; the lowest lane of a collision
+// wins), then the rest take any entry they hold.
+// nb = banks one load instruction spreads over (128 / bytes per gathered
+// value, at least 2); phase = lanes per bank phase (128 / min(bytes, 16)).
+constexpr int kPermRounds = 4;
+constexpr int kPermWarps = 8;
+constexpr int kPermChunks = kBlk;   // chunks per lane and block: 32 entries, one bit each
+
+__global__ void __launch_bounds__(kPermWarps * 32)
+    k_plan_permute(uint16_t *__restrict__ idx16, const uint32_t *__restrict__ cb_all,
+                   const int32_t *__restrict__ split, int64_t nseg, int T, int nwt, int nb, int phase) {
+    __shared__ uint16_t ent_s[kPermWarps][32][kPermChunks * 8];
+    __shared__ uint32_t bm_s[kPermWarps][32][32];   // per lane and bank: unplaced entries (bit i = ent[i])
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kPermWarps + wl;   // simulated warp: tile t, warp k
+    if (gw >= (int64_t)T * nwt) return;
+    const int t = (int)(gw / nwt), k = (int)(gw - (int64_t)t * nwt);
+    const int sA = split[(int64_t)t * (nwt + 1) + k], sB = split[(int64_t)t * (nwt + 1) + k + 1];
+    const uint32_t *__restrict__ cb = cb_all + (int64_t)t * nseg;
+    uint4 *__restrict__ w4 = reinterpret_cast<uint4 *>(idx16);
+    const unsigned phase_lanes = phase >= 32 ? kFull : (((1u << phase) - 1u) << (lane & ~(phase - 1)));
+    uint16_t *ent = ent_s[wl][lane];
+    uint32_t *bm = bm_s[wl][lane];
+    if (sA >= sB) return;
+    const int lg = lanes_log2(cb[sB] - cb[sA], (uint32_t)(sB - sA));
+    const int spr = 32 >> lg, sub = lane >> lg, ln = lane & ((1 << lg) - 1);
+    for (int base = sA; base < sB; base += spr) {
+        const int seg = base + sub;
+        const uint32_t q0 = seg < sB ? cb[seg] : 0u, q1 = seg < sB ? cb[seg + 1] : 0u;
+        const uint32_t m = __reduce_max_sync(kFull, q1 - q0);
+        const uint32_t nch = (m + (1u << lg) - 1) >> lg;   // chunks per lane
+        const uint32_t nwin = (nch + kPermChunks - 1) / kPermChunks;
+        for (uint32_t win = 0; win < nwin; ++win) {
+            // the lane's chunk u of this block: q + u G
+            const uint32_t q = q0 + (uint32_t)ln + ((win * kPermChunks) << lg);
+            unsigned vmask = 0;   // valid chunk slots u of this window
+#pragma unroll
+            for (int u = 0; u < kPermChunks; ++u) {
+                const uint32_t c = q + ((uint32_t)u << lg);
+                if (c < q1) {
+                    vmask |= 1u << u;
+                    const uint4 w = w4[c];
+                    const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        ent[u * 8 + 2 * h] = (uint16_t)(wd[h] & 0xffffu);
+                        ent[u * 8 + 2 * h + 1] = (uint16_t)(wd[h] >> 16);
+                    }
+                }
+            }
+            for (int b = 0; b < nb; ++b) bm[b] = 0u;
+            uint32_t rem = 0;   // entries not yet placed (bit i = ent[i])
+#pragma unroll
+            for (int u = 0; u < kPermChunks; ++u)
+                if (vmask >> u & 1u) rem |= 0xffu << (u * 8);
+            uint32_t have = 0;   // banks this lane still holds
+            for (int i = 0; i < kPermChunks * 8; ++i) {
+                if (rem >> i & 1u) {
+                    const int b = ent[i] & (nb - 1);
+                    bm[b] |= 1u << i;
+                    have |= 1u << b;
+                }
+            }
+            uint16_t placed[kPermChunks * 8];
+            for (int slot = 0; slot < kPermChunks * 8; ++slot) {
+                const int u = slot >> 3;
+                const bool part = (vmask >> u) & 1u;
+                if (!__any_sync(kFull, part)) continue;
+                bool done = !part;
+                int pick = -1;
+                uint32_t taken = 0;   // banks claimed in this lane's phase
+                for (int r = 0; r < kPermRounds; ++r) {
+                    int prop = -1;
+                    const uint32_t av = have & ~taken;
+                    if (!done && av) {
+                        const int rot = (lane * 7 + slot * 3 + r * 5) & (nb - 1);
+                        // first bank at or after rot (cyclically) among av
+                        const uint32_t hi = av & (~0u << rot), lo = av & ~(~0u << rot);
+                        prop = hi ? (__ffs(hi) - 1) : (__ffs(lo) - 1);
+                    }
+                    const unsigned same = __match_any_sync(kFull, prop < 0 ? -1 - lane : prop);
+                    const unsigned peers = same & phase_lanes;
+                    const bool win_ = prop >= 0 && (__ffs(peers) - 1) == lane;
+                    uint32_t claim = win_ ? (1u << prop) : 0u;
+                    for (int o = phase >> 1; o > 0; o >>= 1) claim |= __shfl_xor_sync(kFull, claim, o);
+                    taken |= claim;
+                    if (win_) {
+                        done = true;
+                        pick = prop;
+                    }
+                }
+                if (part) {
+                    const int b0 = pick >= 0 ? pick : (ent[__ffs(rem) - 1] & (nb - 1));
+                    const int i = __ffs(bm[b0]) - 1;
+                    bm[b0] &= ~(1u << i);
+                    if (!bm[b0]) have &= ~(1u << b0);
+                    rem &= ~(1u << i);
+                    placed[slot] = ent[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPermChunks; ++u) {
+                if (vmask >> u & 1u) {
+                    uint4 w;
+                    w.x = (uint32_t)placed[u * 8 + 0] | ((uint32_t)placed[u * 8 + 1] << 16);
+                    w.y = (uint32_t)placed[u * 8 + 2] | ((uint32_t)placed[u * 8 + 3] << 16);
+                    w.z = (uint32_t)placed[u * 8 + 4] | ((uint32_t)placed[u * 8 + 5] << 16);
+                    w.w = (uint32_t)placed[u * 8 + 6] | ((uint32_t)placed[u * 8 + 7] << 16);
+                    w4[q + ((uint32_t)u << lg)] = w;
+                }
+            }
+        }
+    }
+}
+
 __global__ void k_plan_order_keys(const int64_t *__restrict__ col_ptr, int64_t p,
                                   int32_t *__restrict__ keys, int32_t *__restrict__ vals) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
@@ -110,18 +285,12 @@ __global__ void k_plan_order_keys(const int64_t *__restrict__ col_ptr, int64_t p
     }
 }
 
-static int pick_lanes(double mean_chunks) {
-    // about four chunks per lane, many segments in flight per warp
-    if (mean_chunks >= 128) return 32;
-    if (mean_chunks >= 48) return 16;
-    if (mean_chunks >= 20) return 8;
-    return 4;
-}
-
-// Builds one side of the plan: padded tile-major indices and chunk bounds.
+// Builds one side of the plan: padded tile-major indices, chunk bounds and
+// the per-warp work split.
 static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr,
-                            const int32_t *idx, int64_t nseg, int64_t nnz, int W, int T,
-                            uint16_t **out_idx, uint32_t **out_cb, double *mean_chunks) {
+                            const int32_t *idx, const int32_t *order, int64_t nseg, int64_t nnz, int W,
+                            int T, int nwt, int value_bytes, bool bank_order, uint16_t **out_idx,
+                            uint32_t **out_cb, int32_t **out_split, uint32_t *out_sent) {
     cudaError_t e;
     const int64_t nb = (int64_t)(T + 1) * nseg;
     uint32_t *bounds = (uint32_t *)grow(ctx, tag + ":bounds", sizeof(uint32_t) * nb, &e);
@@ -131,8 +300,10 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
     if (!chunks) return cuda_error(ctx, e, "allocating the tiled plan");
     uint32_t *cb = (uint32_t *)grow(ctx, tag + ":cb", sizeof(uint32_t) * nc, &e);
     if (!cb) return cuda_error(ctx, e, "allocating the tiled plan");
-    // at most 7 pad slots per segment
-    const int64_t cap = nnz + 7 * (int64_t)T * nseg + 8;
+    int32_t *split = (int32_t *)grow(ctx, tag + ":split", sizeof(int32_t) * (size_t)T * (nwt + 1), &e);
+    if (!split) return cuda_error(ctx, e, "allocating the tiled plan");
+    // at most 7 pad slots per segment, then the sentinel chunk
+    const int64_t cap = ((nnz + 7 * (int64_t)T * nseg + 7) & ~int64_t(7)) + 8;
     uint16_t *pidx = (uint16_t *)grow(ctx, tag + ":idx", sizeof(uint16_t) * cap, &e);
     if (!pidx) return cuda_error(ctx, e, "allocating the tiled plan");
     size_t tmp_bytes = 0;
@@ -141,30 +312,43 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
     if (!tmp) return cuda_error(ctx, e, "allocating the plan scan");
     const int grid = grid_for(ctx, 256, 8);
     cudaStream_t s = ctx->stream;
-    PCG_PROF(ctx, "plan_bounds", k_plan_bounds<<<grid, 256, 0, s>>>(ptr, idx, nseg, W, T, bounds));
+    PCG_PROF(ctx, "plan_bounds", k_plan_bounds<<<grid, 256, 0, s>>>(ptr, idx, order, nseg, W, T, bounds));
     PCG_PROF(ctx, "plan_chunks", k_plan_chunks<<<grid, 256, 0, s>>>(bounds, nseg, T, chunks));
     PCG_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, chunks, cb, (int)nc, s));
     PCG_PROF(ctx, "plan_fill", k_plan_fill<<<grid, 256, 0, s>>>(idx, bounds, cb, nseg, T, W, pidx));
+    const uint32_t sent = (uint32_t)(cap / 8 - 1);
+    k_plan_sentinel<<<1, 32, 0, s>>>(pidx + (size_t)sent * 8, W);
+    PCG_PROF(ctx, "plan_split", k_plan_split<<<grid_for(ctx, 256, 1), 256, 0, s>>>(cb, nseg, T, nwt, split));
+    if (bank_order) {
+        const int nb = std::max(2, 128 / value_bytes), phase = 128 / std::min(value_bytes, 16);
+        const int64_t sim = (int64_t)T * nwt;
+        const int blocks = (int)((sim + kPermWarps - 1) / kPermWarps);
+        PCG_PROF(ctx, "plan_permute",
+                 k_plan_permute<<<blocks, kPermWarps * 32, 0, s>>>(pidx, cb, split, nseg, T, nwt, nb, phase));
+    }
     PCG_CUDA_TRY(ctx, cudaGetLastError());
     *out_idx = pidx;
     *out_cb = cb;
-    *mean_chunks = (double)(nnz + 3.5 * (double)T * nseg) / 8.0 / ((double)T * nseg);
+    *out_split = split;
+    *out_sent = sent;
     return PCG_OK;
 }
 
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
-                            int RG, int vtype, TiledPlan *pl) {
+                            int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl) {
     *pl = TiledPlan{};
     const int vsize = vtype == kVtF32 ? 4 : 8;   // staged bytes per value (DF: two floats)
     pl->vtype = vtype;
     const int64_t n = Xr->n, p = Xr->p, nnz = Xr->nnz;
     // positions are 32-bit inside the kernels (padding included)
     if (n <= 0 || p <= 0 || nnz <= 0 || nnz + 8 * (n + p) * 4 >= (int64_t)0xfffffff0ll) return PCG_OK;
+    if (n >= (int64_t)INT32_MAX || p >= (int64_t)INT32_MAX) return PCG_OK;
     int64_t w = (kTileSmemBytes - RG * vsize) / (RG * vsize);   // one slot is the zero sentinel
     w = std::min<int64_t>(w, 65528);
     w &= ~int64_t(7);
     pl->RG = RG;
     pl->vsize = vsize;
+    pl->ngroups = std::max(1, ngroups);
     pl->n = n;
     pl->p = p;
     pl->nnz = nnz;
@@ -172,17 +356,26 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     pl->T_c = (int)((p + pl->W_c - 1) / pl->W_c);
     pl->W_r = (int)std::min<int64_t>(w, n);
     pl->T_r = (int)((n + pl->W_r - 1) / pl->W_r);
+    // launch shapes: per group one wave of CTAs over the tiles (strips)
+    const size_t smem_c = (size_t)(pl->W_c + 1) * RG * vsize, smem_r = (size_t)(pl->W_r + 1) * RG * vsize;
+    const int occ_c = std::max(1, std::min(2, (int)(kSmemPerSm / (smem_c + 2048))));
+    const int occ_r = std::max(1, std::min(2, (int)(kSmemPerSm / (smem_r + 2048))));
+    pl->threads = tiled_threads(RG * vsize);
+    pl->nw = pl->threads / 32;
+    pl->csr_blocks = std::max(1, ctx->num_sms * occ_c / pl->T_c);
+    pl->csr_blocks = (int)std::min<int64_t>(pl->csr_blocks, std::max<int64_t>(1, n / (2 * pl->nw)));
+    pl->csc_chunks = std::max(1, ctx->num_sms * occ_r / pl->T_r);
+    pl->csc_chunks = (int)std::min<int64_t>(pl->csc_chunks, std::max<int64_t>(1, p / (2 * pl->nw)));
+    pl->smem_c = smem_c;
+    pl->smem_r = smem_r;
     std::string t(tag);
-    double mc_r = 0, mc_c = 0;
-    pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, n, nnz, pl->W_c, pl->T_c,
-                              &pl->col16, &pl->rt, &mc_r);
-    if (st != PCG_OK) return st;
-    st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, p, nnz, pl->W_r, pl->T_r, &pl->row16,
-                   &pl->cs, &mc_c);
-    if (st != PCG_OK) return st;
+    // the bank-aware entry order costs tens of products' time: only for plans
+    // that serve a whole solve
+    const bool bank_order = ctx->bank_permute && many_products;
     cudaError_t e;
     {
-        // column order by decreasing length for the CSC pass
+        // column order by decreasing length: the CSC pass visits columns in
+        // this order, so the segments a warp holds have similar lengths
         int32_t *keys = (int32_t *)grow(ctx, t + ":ord_keys", sizeof(int32_t) * 2 * p, &e);
         if (!keys) return cuda_error(ctx, e, "allocating the column order");
         int32_t *vals = (int32_t *)grow(ctx, t + ":ord_vals", sizeof(int32_t) * 2 * p, &e);
@@ -198,37 +391,31 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
         PCG_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairsDescending(tmp, tb, keys, keys + p, vals, vals + p,
                                                                     (int)p, 0, 32, ctx->stream));
     }
-    // partial sums: float for float values, double otherwise (DF included)
-    pl->Pr = grow(ctx, t + ":Pr", (size_t)vsize * RG * (size_t)pl->T_c * n, &e);
+    pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, nullptr, n, nnz, pl->W_c, pl->T_c,
+                              pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt, &pl->split_r,
+                              &pl->sent_r);
+    if (st != PCG_OK) return st;
+    st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, pl->col_order, p, nnz, pl->W_r, pl->T_r,
+                   pl->csc_chunks * pl->nw, RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c,
+                   &pl->sent_c);
+    if (st != PCG_OK) return st;
+    // partial sums: float for float values, double otherwise (DF included);
+    // row partials per group, column partials of one group (callers with
+    // several groups pass their own column-partial array)
+    pl->Pr = grow(ctx, t + ":Pr", (size_t)vsize * RG * (size_t)pl->T_c * n * pl->ngroups, &e);
     if (!pl->Pr) return cuda_error(ctx, e, "allocating the tiled partials");
     pl->Pc = grow(ctx, t + ":Pc", (size_t)vsize * RG * (size_t)pl->T_r * p, &e);
     if (!pl->Pc) return cuda_error(ctx, e, "allocating the tiled partials");
-    // launch shapes: one wave of CTAs, rows and columns split evenly (their
-    // nonzero counts then differ by a few percent for these designs)
-    const size_t smem_c = (size_t)(pl->W_c + 1) * RG * vsize, smem_r = (size_t)(pl->W_r + 1) * RG * vsize;
-    const int occ_c = std::max(1, std::min(4, (int)(kSmemPerSm / (smem_c + 4096))));
-    const int occ_r = std::max(1, std::min(4, (int)(kSmemPerSm / (smem_r + 4096))));
-    // one CTA per SM when the staged slice fills its shared memory: give it
-    // 1024 threads so that enough index loads are in flight
-    pl->threads = (occ_c == 1 || occ_r == 1) ? 1024 : 512;
-    pl->csr_blocks = std::max(1, ctx->num_sms * occ_c / pl->T_c);
-    pl->csr_blocks = (int)std::min<int64_t>(pl->csr_blocks, (n + 31) / 32);
-    pl->csc_chunks = std::max(1, ctx->num_sms * occ_r / pl->T_r);
-    pl->csc_chunks = (int)std::min<int64_t>(pl->csc_chunks, std::max<int64_t>(1, p / 32));
-    pl->G_row = pick_lanes(mc_r);
-    pl->G_col = pick_lanes(mc_c);
-    pl->smem_c = smem_c;
-    pl->smem_r = smem_r;
     pl->valid = true;
     return PCG_OK;
 }
 
 // ---------------------------------------------------------------------------
 // value types.  float and double are gathered and summed as themselves.  DF
-// ("double-float") holds each value as an unevaluated pair hi + lo of floats
-// (about 48 significant bits) and sums with the error-free TwoSum, so float
-// arithmetic reaches float64-like accuracy (GB300 runs float64 at a small
-// fraction of its float32 rate).
+// ("double-float", df.cuh) holds each value as a pair hi + lo of floats and
+// sums with TwoSum, so float arithmetic reaches float64-like accuracy; its
+// sources (s, omega), staged values and partial sums are all float pairs, so
+// the products run no float64 instruction.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Tr;
@@ -247,106 +434,118 @@ struct Tr<double> {
 template <>
 struct Tr<DF> {
     using smem = float2;
-    using part = double;
-    using src = double;
+    using part = float2;
+    using src = float2;
 };
 
-template <typename T>
-__device__ __forceinline__ typename Tr<T>::smem to_smem(typename Tr<T>::src x) { return x; }
-template <>
-__device__ __forceinline__ float2 to_smem<DF>(double x) {
-    const float hi = __double2float_rn(x);
-    return make_float2(hi, __double2float_rn(x - (double)hi));
-}
 template <typename T>
 __device__ __forceinline__ typename Tr<T>::smem smem_zero() { return typename Tr<T>::smem(0); }
 template <>
 __device__ __forceinline__ float2 smem_zero<DF>() { return make_float2(0.f, 0.f); }
+template <typename T>
+__device__ __forceinline__ typename Tr<T>::src src_zero() { return typename Tr<T>::src(0); }
+template <>
+__device__ __forceinline__ float2 src_zero<DF>() { return make_float2(0.f, 0.f); }
 
-// s + x = t + e exactly (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float &t, float &e) {
-    t = __fadd_rn(a, b);
-    const float bv = __fsub_rn(t, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bv)), __fsub_rn(b, bv));
-}
+// u = omega * (sum of row partials), in the staged type
+__device__ __forceinline__ float scale_part(float o, float a) { return o * a; }
+__device__ __forceinline__ double scale_part(double o, double a) { return o * a; }
+__device__ __forceinline__ float2 scale_part(float2 o, float2 a) { return df_mul(o, a); }
 
+// Accumulators of RG sums, in two independent sets (entries alternate between
+// them, so consecutive additions do not wait on each other).
 template <typename T, int RG>
 struct Vec {
-    T v[RG];
+    T v[2][RG];
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int r = 0; r < RG; ++r) v[r] = T(0);
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) v[k][r] = T(0);
     }
+    template <int K>
     __device__ __forceinline__ void add_smem(const T *base) {   // base: shared memory
         if constexpr (sizeof(T) == 4 && RG % 4 == 0) {
 #pragma unroll
             for (int r = 0; r < RG; r += 4) {
                 const float4 x = *reinterpret_cast<const float4 *>(base + r);
-                v[r] += x.x; v[r + 1] += x.y; v[r + 2] += x.z; v[r + 3] += x.w;
+                v[K][r] += x.x; v[K][r + 1] += x.y; v[K][r + 2] += x.z; v[K][r + 3] += x.w;
             }
         } else if constexpr (sizeof(T) == 4 && RG == 2) {
             const float2 x = *reinterpret_cast<const float2 *>(base);
-            v[0] += x.x; v[1] += x.y;
+            v[K][0] += x.x; v[K][1] += x.y;
         } else if constexpr (sizeof(T) == 8 && RG % 2 == 0) {
 #pragma unroll
             for (int r = 0; r < RG; r += 2) {
                 const double2 x = *reinterpret_cast<const double2 *>(base + r);
-                v[r] += x.x; v[r + 1] += x.y;
+                v[K][r] += x.x; v[K][r + 1] += x.y;
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < RG; ++r) v[r] += base[r];
+            for (int r = 0; r < RG; ++r) v[K][r] += base[r];
         }
     }
-    template <int G>
-    __device__ __forceinline__ void reduce() {
+    // merges the two sets, then sums over aligned groups of 2^lg lanes
+    // (every lane of the warp calls it)
+    __device__ __forceinline__ void reduce(int lg) {
 #pragma unroll
-        for (int r = 0; r < RG; ++r) v[r] = group_sum<G>(v[r]);
+        for (int r = 0; r < RG; ++r) v[0][r] += v[1][r];
+        for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int r = 0; r < RG; ++r) v[0][r] += __shfl_xor_sync(kFull, v[0][r], o);
+        }
     }
-    __device__ __forceinline__ T out(int r) const { return v[r]; }
+    __device__ __forceinline__ T out(int r) const { return v[0][r]; }
 };
 
 template <int RG>
 struct Vec<DF, RG> {
-    float s[RG], c[RG];   // running sum and its accumulated rounding errors
+    float s[2][RG], c[2][RG];   // running sums and their accumulated rounding errors
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int r = 0; r < RG; ++r) s[r] = c[r] = 0.f;
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) s[k][r] = c[k][r] = 0.f;
     }
+    template <int K>
     __device__ __forceinline__ void add1(int r, float2 x) {
         float t, e;
-        two_sum(s[r], x.x, t, e);
-        s[r] = t;
-        c[r] += e + x.y;
+        two_sum(s[K][r], x.x, t, e);
+        s[K][r] = t;
+        c[K][r] += e + x.y;
     }
+    template <int K>
     __device__ __forceinline__ void add_smem(const float2 *base) {
         if constexpr (RG % 2 == 0) {
 #pragma unroll
             for (int r = 0; r < RG; r += 2) {
                 const float4 x = *reinterpret_cast<const float4 *>(base + r);
-                add1(r, make_float2(x.x, x.y));
-                add1(r + 1, make_float2(x.z, x.w));
+                add1<K>(r, make_float2(x.x, x.y));
+                add1<K>(r + 1, make_float2(x.z, x.w));
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < RG; ++r) add1(r, base[r]);
+            for (int r = 0; r < RG; ++r) add1<K>(r, base[r]);
         }
     }
-    template <int G>
-    __device__ __forceinline__ void reduce() {
+    __device__ __forceinline__ void merge2(float &s0, float &c0, float s1, float c1) {
+        float t, e;
+        two_sum(s0, s1, t, e);
+        s0 = t;
+        c0 += c1 + e;
+    }
+    __device__ __forceinline__ void reduce(int lg) {
 #pragma unroll
-        for (int r = 0; r < RG; ++r) {
+        for (int r = 0; r < RG; ++r) merge2(s[0][r], c[0][r], s[1][r], c[1][r]);
+        for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) {
-                const float os = __shfl_xor_sync(kFull, s[r], o), oc = __shfl_xor_sync(kFull, c[r], o);
-                float t, e;
-                two_sum(s[r], os, t, e);
-                s[r] = t;
-                c[r] += oc + e;
+            for (int r = 0; r < RG; ++r) {
+                const float os = __shfl_xor_sync(kFull, s[0][r], o), oc = __shfl_xor_sync(kFull, c[0][r], o);
+                merge2(s[0][r], c[0][r], os, oc);
             }
         }
     }
-    __device__ __forceinline__ double out(int r) const { return (double)s[r] + (double)c[r]; }
+    __device__ __forceinline__ float2 out(int r) const { return df_norm(s[0][r], c[0][r]); }
 };
 
 // Adds the gathered values of one whole chunk of 8 indices (pad slots point
@@ -357,156 +556,215 @@ __device__ __forceinline__ void chunk_add(const uint4 w, const typename Tr<T>::s
     const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-        acc.add_smem(sv + (wd[h] & 0xffffu) * RG);
-        acc.add_smem(sv + (wd[h] >> 16) * RG);
+        acc.template add_smem<0>(sv + (wd[h] & 0xffffu) * RG);
+        acc.template add_smem<1>(sv + (wd[h] >> 16) * RG);
     }
 }
 
-// Chunks [q0, q1) of one padded segment by a group of G lanes, four 16-byte
-// chunk loads in flight per lane.  Every lane of the warp runs the same number
-// of rounds (the most any group of the warp needs), the surplus chunks masked,
-// so groups never split the warp into separate paths.  All 32 lanes must call
-// it (an idle group passes q0 = q1).
-template <typename T, int RG, int G>
-__device__ __forceinline__ void segment_smem_sum(const uint16_t *__restrict__ idx16, uint32_t q0,
-                                                 uint32_t q1, const typename Tr<T>::smem *__restrict__ sv,
-                                                 Vec<T, RG> &acc, int lane) {
-    const uint4 *__restrict__ w4 = reinterpret_cast<const uint4 *>(idx16);
-    const uint32_t rounds = (q1 - q0 + G - 1) / G;
-    const uint32_t wr = __reduce_max_sync(kFull, rounds);
-    uint32_t q = q0 + lane;
-    for (uint32_t t = 0; t < wr; t += 4, q += 4 * G) {
-        const bool va = q < q1, vb = q + G < q1, vc = q + 2 * G < q1, vd = q + 3 * G < q1;
-        uint4 a = {}, b = {}, c = {}, d = {};
-        if (va) a = __ldcs(w4 + q);
-        if (vb) b = __ldcs(w4 + q + G);
-        if (vc) c = __ldcs(w4 + q + 2 * G);
-        if (vd) d = __ldcs(w4 + q + 3 * G);
-        if (va) chunk_add<T, RG>(a, sv, acc);
-        if (vb) chunk_add<T, RG>(b, sv, acc);
-        if (vc) chunk_add<T, RG>(c, sv, acc);
-        if (vd) chunk_add<T, RG>(d, sv, acc);
+// One warp sums the segments [sA, sB) of a tile (rows of a column tile, or
+// columns of a row strip, in their stored order), G lanes per segment: lane
+// ln of a group reads the segment's chunks q0 + ln + G j (a group reads G
+// consecutive 16-byte chunks per load) and adds the staged values their
+// entries name; the group's lanes are summed at the end.  G (2 to 32) is
+// chosen per warp so that a typical segment of its range takes one block of
+// kBlk chunks per lane.  The warp runs in rounds of 32 / G consecutive
+// segments; in a round every group runs the same number of chunks (the
+// round's longest segment: the CSR rows have similar lengths and the CSC
+// columns are stored by decreasing length), a lane past its segment's end
+// reading the sentinel chunk (all zero values).  The next block (of this
+// round, or the first of the next round) is loaded before the current one is
+// summed, so 2 kBlk chunks per lane are in flight.  Segment s's chunks are
+// [cb[s], cb[s + 1]); its sum goes to out[(keys ? keys[s] : s) * ostride + r].
+struct SegRound {
+    uint32_t q0, q1;   // this lane's segment's chunks
+    int64_t key;
+    uint32_t nch;      // chunks per lane in this round (uniform over the warp)
+};
+
+__device__ __forceinline__ SegRound load_round(const uint32_t *__restrict__ cb, const int32_t *__restrict__ keys,
+                                               int base, int sB, int sub) {
+    SegRound R;
+    const int seg = base + sub;
+    R.q0 = R.q1 = 0;
+    R.key = seg;
+    if (seg < sB) {
+        R.q0 = __ldg(cb + seg);
+        R.q1 = __ldg(cb + seg + 1);
+        if (keys) R.key = __ldg(keys + seg);
+    }
+    R.nch = 0;
+    return R;
+}
+
+__device__ __forceinline__ uint32_t round_chunks(const SegRound &R, int lg) {
+    const uint32_t m = __reduce_max_sync(kFull, R.q1 - R.q0);
+    return (m + (1u << lg) - 1) >> lg;
+}
+
+__device__ __forceinline__ void load_block(uint4 (&A)[kBlk], const uint4 *__restrict__ w4, const SegRound &R,
+                                           uint32_t j, int ln, int lg, uint32_t sent) {
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) {
+        const uint32_t c = R.q0 + (uint32_t)ln + ((j + (uint32_t)u) << lg);
+        A[u] = w4[c < R.q1 ? c : sent];
+    }
+}
+
+template <typename T, int RG>
+__device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, const uint32_t *__restrict__ cb,
+                                              int sA, int sB, const typename Tr<T>::smem *__restrict__ sv,
+                                              uint32_t sent, const int32_t *__restrict__ keys,
+                                              typename Tr<T>::part *__restrict__ out, int64_t ostride) {
+    if (sA >= sB) return;
+    const int lane = threadIdx.x & 31;
+    const int lg = lanes_log2(__ldg(cb + sB) - __ldg(cb + sA), (uint32_t)(sB - sA));
+    const int spr = 32 >> lg, sub = lane >> lg, ln = lane & ((1 << lg) - 1);
+    SegRound cur = load_round(cb, keys, sA, sB, sub);
+    cur.nch = round_chunks(cur, lg);
+    SegRound nxt = load_round(cb, keys, sA + spr, sB, sub);
+    int base = sA;
+    uint32_t j = 0;
+    uint4 A[kBlk];
+    load_block(A, w4, cur, 0, ln, lg, sent);
+    Vec<T, RG> acc;
+    acc.zero();
+    for (;;) {
+        // the block after this one: in this round, or the first of the next
+        const bool last = j + kBlk >= cur.nch;
+        if (last && base + spr < sB) nxt.nch = round_chunks(nxt, lg);
+        uint4 B[kBlk];
+        if (!last) load_block(B, w4, cur, j + kBlk, ln, lg, sent);
+        else load_block(B, w4, nxt, 0, ln, lg, sent);
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u)
+            if (j + (uint32_t)u < cur.nch) chunk_add<T, RG>(A[u], sv, acc);
+        if (last) {
+            acc.reduce(lg);
+            if (base + sub < sB && ln == 0) {
+#pragma unroll
+                for (int r = 0; r < RG; ++r) out[cur.key * ostride + r] = acc.out(r);
+            }
+            acc.zero();
+            base += spr;
+            if (base >= sB) break;
+            cur = nxt;
+            nxt = load_round(cb, keys, base + spr, sB, sub);
+            j = 0;
+        } else {
+            j += kBlk;
+        }
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u) A[u] = B[u];
     }
 }
 
 // ---------------------------------------------------------------------------
-// CSR pass: blockIdx.x = c * csr_blocks + b
-// S: global gather source, element (j, r) at S[j * s_stride + s_off + r]
+// CSR pass: blockIdx.x = c * csr_blocks + b, blockIdx.y = RHS group g.
+// S: global gather source, element (j, r) of group g at
+// S[j * s_stride + s_off + g * RG + r].  Skipped when gate[g] != gate_need.
+// Writes the row partials of tile c: Pr[g][c][i][r].
 // ---------------------------------------------------------------------------
-template <typename T, int RG, int G>
-__global__ void __launch_bounds__(1024) k_t_csr(TiledArgs A, const typename Tr<T>::src *__restrict__ S,
-                                               int s_stride, int s_off, const int *gate, int gate_need) {
+constexpr int kStageUnroll = 8;    // CSR staging: values in flight per thread
+constexpr int kStageUnrollC = 4;   // CSC staging (each value needs T_c + 1 loads)
+
+template <typename T, int RG>
+__global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
+    k_t_csr(TiledArgs A, const typename Tr<T>::src *__restrict__ S, int s_stride, int s_off, const int *gate,
+            int gate_need) {
     using SM = typename Tr<T>::smem;
     using PT = typename Tr<T>::part;
+    using SRC = typename Tr<T>::src;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (gate && (*(volatile const int *)gate) != gate_need) return;
+    const int g = blockIdx.y;
+    if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
     SM *sS = reinterpret_cast<SM *>(smem_raw);
     const TiledPlan &P = A.plan;
     const int c = blockIdx.x / P.csr_blocks, b = blockIdx.x % P.csr_blocks;
     const int64_t j0 = (int64_t)c * P.W_c;
-    const int64_t ext = min((int64_t)P.W_c, P.p - j0);
-    for (int64_t t = threadIdx.x; t < ext * RG; t += blockDim.x) {
-        const int64_t j = t / RG;
-        const int r = (int)(t - j * RG);
-        sS[t] = to_smem<T>(S[(j0 + j) * s_stride + s_off + r]);
+    const int64_t total = min((int64_t)P.W_c, P.p - j0) * RG;
+    const int off = s_off + g * RG;
+    // stage the tile's slice of s, kStageUnroll loads in flight per thread
+    for (int64_t t0 = threadIdx.x; t0 < total; t0 += (int64_t)kStageUnroll * blockDim.x) {
+        SRC v[kStageUnroll];
+#pragma unroll
+        for (int k = 0; k < kStageUnroll; ++k) {
+            const int64_t t = t0 + (int64_t)k * blockDim.x;
+            v[k] = t < total ? __ldg(S + (j0 + t / RG) * s_stride + off + (int)(t % RG)) : src_zero<T>();
+        }
+#pragma unroll
+        for (int k = 0; k < kStageUnroll; ++k) {
+            const int64_t t = t0 + (int64_t)k * blockDim.x;
+            if (t < total) sS[t] = v[k];
+        }
     }
     if (threadIdx.x < RG) sS[(size_t)P.W_c * RG + threadIdx.x] = smem_zero<T>();   // pad sentinel
     __syncthreads();
-    const int64_t n = P.n;
-    const int64_t i0 = n * b / P.csr_blocks, i1 = n * (b + 1) / P.csr_blocks;
-    const int lane = threadIdx.x & (G - 1);
-    const int gpw = 32 / G;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int sub = (threadIdx.x & 31) / G;
-    // chunk bounds of tile c: row i's chunks are [rb[i], rb[i + 1])
-    const uint32_t *__restrict__ rb = P.rt + (size_t)c * n;
-    PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + (size_t)c * n * RG;
-    const int64_t step = (int64_t)nw * gpw;
-    int64_t base = i0 + (int64_t)warp * gpw;
-    int64_t i = base + sub;
-    uint32_t a0 = i < i1 ? __ldg(rb + i) : 0u, a1 = i < i1 ? __ldg(rb + i + 1) : 0u;
-    for (; base < i1; base += step) {
-        // bounds of this group's next row, loaded while this row is summed
-        const int64_t in = i + step;
-        const uint32_t b0 = in < i1 ? __ldg(rb + in) : 0u, b1 = in < i1 ? __ldg(rb + in + 1) : 0u;
-        Vec<T, RG> acc;
-        acc.zero();
-        segment_smem_sum<T, RG, G>(P.col16, i < i1 ? a0 : 0u, i < i1 ? a1 : 0u, sS, acc, lane);
-        acc.template reduce<G>();
-        if (i < i1 && lane == 0) {
-#pragma unroll
-            for (int r = 0; r < RG; ++r) Pr[(size_t)i * RG + r] = acc.out(r);
-        }
-        i = in;
-        a0 = b0;
-        a1 = b1;
-    }
+    const int warp = threadIdx.x >> 5;
+    const int32_t *__restrict__ sp = P.split_r + (size_t)c * (P.csr_blocks * P.nw + 1) + b * P.nw + warp;
+    const int sA = __ldg(sp), sB = __ldg(sp + 1);
+    PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + ((size_t)g * P.T_c + c) * (size_t)P.n * RG;
+    warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.col16), P.rt + (size_t)c * P.n, sA, sB, sS,
+                         P.sent_r, nullptr, Pr, RG);
 }
 
 // ---------------------------------------------------------------------------
-// CSC pass: blockIdx.x = t * csc_chunks + h.  Stages u = om (.) sum_c Pr[c]
-// for the strip's rows; om element (i, r) at om[i * om_stride + om_off + r].
-// Column partial (t, j, r) goes to pc_out[(t * p + j) * pc_stride + pc_off + r].
+// CSC pass: blockIdx.x = t * csc_chunks + h, blockIdx.y = RHS group g.
+// Stages u = om (.) sum_c Pr[g][c] for the strip's rows; om element (i, r) of
+// group g at om[i * om_stride + om_off + g * RG + r].  Column partial (t, j, r)
+// goes to pc_out[(t * p + j) * pc_stride + pc_off + g * RG + r].
 // ---------------------------------------------------------------------------
-template <typename T, int RG, int G>
-__global__ void __launch_bounds__(1024) k_t_csc(TiledArgs A, const typename Tr<T>::src *__restrict__ om,
-                                               int om_stride, int om_off,
-                                               typename Tr<T>::part *__restrict__ pc_out, int pc_stride,
-                                               int pc_off, const int *gate, int gate_need) {
+template <typename T, int RG>
+__global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
+    k_t_csc(TiledArgs A, const typename Tr<T>::src *__restrict__ om, int om_stride, int om_off,
+            typename Tr<T>::part *__restrict__ pc_out, int pc_stride, int pc_off, const int *gate, int gate_need) {
     using SM = typename Tr<T>::smem;
     using PT = typename Tr<T>::part;
+    using SRC = typename Tr<T>::src;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (gate && (*(volatile const int *)gate) != gate_need) return;
+    const int g = blockIdx.y;
+    if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
     SM *sU = reinterpret_cast<SM *>(smem_raw);
     const TiledPlan &P = A.plan;
     const int t = blockIdx.x / P.csc_chunks, h = blockIdx.x % P.csc_chunks;
     const int64_t n = P.n, p = P.p;
     const int64_t r0 = (int64_t)t * P.W_r;
-    const int64_t ext = min((int64_t)P.W_r, n - r0);
-    const PT *__restrict__ Pr = reinterpret_cast<const PT *>(P.Pr);
-    for (int64_t q = threadIdx.x; q < ext * RG; q += blockDim.x) {
-        const int64_t i = r0 + q / RG;
-        const int r = (int)(q % RG);
-        PT acc = Pr[(size_t)i * RG + r];
-        for (int c = 1; c < P.T_c; ++c) acc += Pr[((size_t)c * n + i) * RG + r];
-        sU[q] = to_smem<T>(om[i * om_stride + om_off + r] * acc);
+    const int64_t total = min((int64_t)P.W_r, n - r0) * RG;
+    const PT *__restrict__ Pr = reinterpret_cast<const PT *>(P.Pr) + (size_t)g * P.T_c * (size_t)n * RG;
+    const int ooff = om_off + g * RG;
+    for (int64_t q0 = threadIdx.x; q0 < total; q0 += (int64_t)kStageUnrollC * blockDim.x) {
+        PT acc[kStageUnrollC];
+        SRC o[kStageUnrollC];
+#pragma unroll
+        for (int k = 0; k < kStageUnrollC; ++k) {
+            const int64_t q = q0 + (int64_t)k * blockDim.x;
+            const bool v = q < total;
+            const int64_t i = r0 + q / RG;
+            const int r = (int)(q % RG);
+            o[k] = v ? __ldg(om + i * om_stride + ooff + r) : src_zero<T>();
+            acc[k] = v ? __ldg(Pr + i * RG + r) : src_zero<T>();
+        }
+        for (int c = 1; c < P.T_c; ++c) {
+#pragma unroll
+            for (int k = 0; k < kStageUnrollC; ++k) {
+                const int64_t q = q0 + (int64_t)k * blockDim.x;
+                if (q < total)
+                    acc[k] = part_add(acc[k], __ldg(Pr + ((size_t)c * n + r0 + q / RG) * RG + (int)(q % RG)));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kStageUnrollC; ++k) {
+            const int64_t q = q0 + (int64_t)k * blockDim.x;
+            if (q < total) sU[q] = scale_part(o[k], acc[k]);
+        }
     }
     if (threadIdx.x < RG) sU[(size_t)P.W_r * RG + threadIdx.x] = smem_zero<T>();   // pad sentinel
     __syncthreads();
-    // the strip's columns in order of decreasing length; this CTA takes every
-    // csc_chunks-th of them, so each CTA gets a mix of lengths and the lane
-    // groups of a warp get columns of similar length
-    const int64_t jA = 0, jB = (p - h + P.csc_chunks - 1) / P.csc_chunks;   // positions h + k * chunks
-    const int lane = threadIdx.x & (G - 1);
-    const int gpw = 32 / G;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int sub = (threadIdx.x & 31) / G;
-    // chunk bounds of strip t: column j's chunks are [cb[j], cb[j + 1])
-    const uint32_t *__restrict__ cb = P.cs + (size_t)t * p;
-    const int32_t *__restrict__ order = P.col_order;
-    PT *__restrict__ Pc = pc_out + (size_t)t * p * pc_stride + pc_off;
-    const int64_t step = (int64_t)nw * gpw;
-    int64_t base = jA + (int64_t)warp * gpw;
-    int64_t k = base + sub;
-    int32_t j = k < jB ? __ldg(order + h + k * P.csc_chunks) : 0;
-    uint32_t a0 = k < jB ? __ldg(cb + j) : 0u, a1 = k < jB ? __ldg(cb + j + 1) : 0u;
-    for (; base < jB; base += step) {
-        const int64_t kn = k + step;
-        const int32_t jn = kn < jB ? __ldg(order + h + kn * P.csc_chunks) : 0;
-        const uint32_t b0 = kn < jB ? __ldg(cb + jn) : 0u, b1 = kn < jB ? __ldg(cb + jn + 1) : 0u;
-        Vec<T, RG> acc;
-        acc.zero();
-        segment_smem_sum<T, RG, G>(P.row16, k < jB ? a0 : 0u, k < jB ? a1 : 0u, sU, acc, lane);
-        acc.template reduce<G>();
-        if (k < jB && lane == 0) {
-#pragma unroll
-            for (int r = 0; r < RG; ++r) Pc[(size_t)j * pc_stride + r] = acc.out(r);
-        }
-        k = kn;
-        j = jn;
-        a0 = b0;
-        a1 = b1;
-    }
+    const int warp = threadIdx.x >> 5;
+    const int32_t *__restrict__ sp = P.split_c + (size_t)t * (P.csc_chunks * P.nw + 1) + h * P.nw + warp;
+    const int sA = __ldg(sp), sB = __ldg(sp + 1);
+    PT *__restrict__ Pc = pc_out + (size_t)t * p * pc_stride + pc_off + g * RG;
+    warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.row16), P.cs + (size_t)t * p, sA, sB, sU,
+                         P.sent_c, P.col_order, Pc, pc_stride);
 }
 
 // ---------------------------------------------------------------------------
@@ -526,9 +784,9 @@ __global__ void __launch_bounds__(256) k_t_fin1(const DrawDesc *__restrict__ d, 
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         T acc = Pc[j];
-        for (int t = 1; t < P.T_r; ++t) acc += Pc[(size_t)t * p + j];
+        for (int t = 1; t < P.T_r; ++t) acc = part_add(acc, Pc[(size_t)t * p + j]);
         const double sj = ws.s64[j];
-        const double v = (double)acc + prior_prec(tau, d->lambda[j]) * sj;
+        const double v = part_to_double(acc) + prior_prec(tau, d->lambda[j]) * sj;
         ws.v64[j] = v;
         sig += sj * v;
     }
@@ -552,57 +810,38 @@ __global__ void __launch_bounds__(256) k_t_fin1(const DrawDesc *__restrict__ d, 
 // ---------------------------------------------------------------------------
 // host: kernel pointers and shared-memory attributes
 // ---------------------------------------------------------------------------
-template <typename T, int RG>
-static void *csr_ptr(int G) {
-    switch (G) {
-        case 4: return (void *)k_t_csr<T, RG, 4>;
-        case 8: return (void *)k_t_csr<T, RG, 8>;
-        case 16: return (void *)k_t_csr<T, RG, 16>;
-        default: return (void *)k_t_csr<T, RG, 32>;
-    }
-}
-template <typename T, int RG>
-static void *csc_ptr(int G) {
-    switch (G) {
-        case 4: return (void *)k_t_csc<T, RG, 4>;
-        case 8: return (void *)k_t_csc<T, RG, 8>;
-        case 16: return (void *)k_t_csc<T, RG, 16>;
-        default: return (void *)k_t_csc<T, RG, 32>;
-    }
-}
-
 template <typename T>
-static void *csr_ptr_rg(int RG, int G) {
+static void *csr_ptr_rg(int RG) {
     switch (RG) {
-        case 1: return csr_ptr<T, 1>(G);
-        case 2: return csr_ptr<T, 2>(G);
-        case 4: return csr_ptr<T, 4>(G);
-        default: return csr_ptr<T, 8>(G);
+        case 1: return (void *)k_t_csr<T, 1>;
+        case 2: return (void *)k_t_csr<T, 2>;
+        case 4: return (void *)k_t_csr<T, 4>;
+        default: return (void *)k_t_csr<T, 8>;
     }
 }
 template <typename T>
-static void *csc_ptr_rg(int RG, int G) {
+static void *csc_ptr_rg(int RG) {
     switch (RG) {
-        case 1: return csc_ptr<T, 1>(G);
-        case 2: return csc_ptr<T, 2>(G);
-        case 4: return csc_ptr<T, 4>(G);
-        default: return csc_ptr<T, 8>(G);
+        case 1: return (void *)k_t_csc<T, 1>;
+        case 2: return (void *)k_t_csc<T, 2>;
+        case 4: return (void *)k_t_csc<T, 4>;
+        default: return (void *)k_t_csc<T, 8>;
     }
 }
 
 TiledKernels tiled_kernels(const TiledPlan &pl) {
     TiledKernels k{};
     if (pl.vtype == kVtF32) {
-        k.csr = csr_ptr_rg<float>(pl.RG, pl.G_row);
-        k.csc = csc_ptr_rg<float>(pl.RG, pl.G_col);
+        k.csr = csr_ptr_rg<float>(pl.RG);
+        k.csc = csc_ptr_rg<float>(pl.RG);
         k.fin1 = (void *)k_t_fin1<float>;
     } else if (pl.vtype == kVtDF) {
-        k.csr = csr_ptr_rg<DF>(pl.RG, pl.G_row);
-        k.csc = csc_ptr_rg<DF>(pl.RG, pl.G_col);
-        k.fin1 = (void *)k_t_fin1<double>;
+        k.csr = csr_ptr_rg<DF>(pl.RG);
+        k.csc = csc_ptr_rg<DF>(pl.RG);
+        k.fin1 = (void *)k_t_fin1<float2>;
     } else {
-        k.csr = csr_ptr_rg<double>(pl.RG, pl.G_row);
-        k.csc = csc_ptr_rg<double>(pl.RG, pl.G_col);
+        k.csr = csr_ptr_rg<double>(pl.RG);
+        k.csc = csc_ptr_rg<double>(pl.RG);
         k.fin1 = (void *)k_t_fin1<double>;
     }
     return k;

@@ -16,23 +16,32 @@ constexpr int kVtF64 = 1;   // double values, double sums
 constexpr int kVtDF = 2;    // double-float pairs summed with TwoSum (float arithmetic)
 struct DF {};
 constexpr size_t kSmemPerSm = 228 * 1024;     // shared memory of one SM
+// threads of a tiled-product CTA (one CTA per SM): 24 warps, or 16 when a
+// gathered value is wider than 16 bytes (more registers per thread)
+constexpr int tiled_threads(int value_bytes) { return value_bytes > 16 ? 512 : 768; }
+constexpr int kBlk = 4;                       // chunks a lane reads per block (two blocks in flight)
+constexpr uint32_t kSegCost = 2;              // work split: cost of a segment in chunks
 
 struct TiledPlan {
     bool valid;
     int RG, vsize, vtype;     // values gathered per nonzero, staged bytes per value, kVt*
+    int ngroups;              // RHS groups sharing the plan (blockIdx.y of the products)
     int64_t n, p, nnz;
     int W_c, T_c;             // column tile width and count (CSR pass)
     int W_r, T_r;             // row strip height and count (CSC pass)
     uint16_t *col16;          // tile-major column offsets inside the tile, each row's run padded
                               // to whole 8-entry chunks with the sentinel W_c
-    uint16_t *row16;          // strip-major row offsets inside the strip, padded likewise (W_r)
+    uint16_t *row16;          // strip-major row offsets inside the strip, columns in col_order,
+                              // padded likewise (W_r)
     uint32_t *rt;             // rt[c * n + i]: first chunk of row i in tile c (T_c * n + 1 entries)
-    uint32_t *cs;             // cs[t * p + j]: first chunk of column j in strip t (T_r * p + 1)
-    int32_t *col_order;       // columns by decreasing length (the CSC pass's work order)
-    void *Pr;                 // row partials [T_c][n][RG]
-    void *Pc;                 // column partials [T_r][p][RG]
-    int csr_blocks, csc_chunks, threads;
-    int G_row, G_col;         // lanes per row / column segment
+    uint32_t *cs;             // cs[t * p + k]: first chunk of column col_order[k] in strip t (T_r * p + 1)
+    int32_t *col_order;       // columns by decreasing length (the CSC pass's segment order)
+    int32_t *split_r;         // [T_c][csr_blocks * nw + 1]: first row of each warp of a column tile
+    int32_t *split_c;         // [T_r][csc_chunks * nw + 1]: first column position of each warp of a strip
+    void *Pr;                 // row partials [ngroups][T_c][n][RG]
+    void *Pc;                 // column partials [T_r][p][RG] (one group)
+    int csr_blocks, csc_chunks, threads, nw;
+    uint32_t sent_r, sent_c;  // the sentinel chunk (8 zero-slot entries) of each index array
     size_t smem_c, smem_r;    // dynamic shared memory of the two passes
 };
 
@@ -44,11 +53,14 @@ struct TiledKernels {
     void *csr, *csc, *fin1;
 };
 
-// Builds (on the context stream) the 16-bit index copies and tile bounds of X
-// for RG values of vsize bytes per gather.  Leaves pl->valid false when the
-// tiled products do not apply (empty X or nnz beyond 32-bit offsets).
+// Builds (on the context stream) the 16-bit index copies, tile bounds and
+// per-warp work split of X for RG values of type vtype per gather and
+// `ngroups` RHS groups; with many_products also the bank-aware entry order
+// (worth its cost only when the plan serves many products).  Leaves
+// pl->valid false when the tiled products do not apply (empty X or nnz beyond
+// 32-bit offsets).
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
-                            int RG, int vtype, TiledPlan *pl);
+                            int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl);
 TiledKernels tiled_kernels(const TiledPlan &pl);
 // kernel pointers plus their dynamic shared-memory attributes
 pcg_status tiled_prepare(pcg_ctx *ctx, const TiledPlan &pl, TiledKernels *k);

@@ -119,6 +119,24 @@ def test_batched_df32_matches_oracle(pb, small3):
         assert rel(beta[r], ref) < 1e-5, r
 
 
+@pytest.mark.parametrize("rg", ["1", "2", "4"])
+def test_batched_df32_every_group_width(pb, small3, rg, monkeypatch):
+    """Double-float products in groups of 1, 2 and 4 right-hand sides (one
+    launch covers every group): per chain, float64-band iteration counts and
+    draws within 1e-5 of the oracle."""
+    monkeypatch.setenv("PCG_BETA_BATCH_RG", rg)
+    P = small3
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    ctx = pb.Context(precision="df32")
+    res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
+    beta = res.beta.cpu().numpy()
+    for r in (0, 3, 8, 15):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
+        assert res.status[r] == pb.PCG_OK and abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (r, res.iters[r], k)
+        assert rel(beta[r], ref) < 1e-5, r
+
+
 def test_batched_fp64_mode_rejected(pb, small3):
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
@@ -144,3 +162,30 @@ def test_batched_full_size_true_residual(pb):
         rt = tau * lam * (b - O.phi_mul(P.X, om, lam, tau, beta[r]))
         assert res.status[r] == pb.PCG_OK
         assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6, r
+
+
+@pytest.mark.slow
+def test_batched_full_size_df32_matches_oracle_samples(pb):
+    """The benchmark's launch (n = 5e5, p = 5e4, 16 chains, double-float
+    products): per chain the status, the iteration count within the float64
+    band of the oracle's, and beta at the oracle's 64 sampled coordinates
+    (tests/golden/config3_oracle.json, written by a script that runs only the
+    oracle) within relative L2 1e-5."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "config3_oracle.json")) as f:
+        gold = json.load(f)
+    P = inputs.config3()
+    if P.X.nnz != gold["nnz"]:
+        pytest.skip("the generated design differs from the one the golden file was made from")
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    ctx = pb.Context(precision="df32")
+    res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=20_000)
+    beta = res.beta.cpu().numpy()
+    for g in gold["chains"]:
+        r, k = g["chain"], g["iters"]
+        idx = np.asarray(g["sample_idx"])
+        ref = np.asarray(g["beta_sample"])
+        assert res.status[r] == pb.PCG_OK, r
+        assert abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (r, res.iters[r], k)
+        assert rel(beta[r][idx], ref) < 1e-5, r

@@ -285,3 +285,20 @@ def test_repeat_calls_deterministic(pb, cfg2):
     b1 = r1.beta.clone()
     r2 = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"])
     assert r1.iters == r2.iters and torch.equal(b1, r2.beta)
+
+
+def test_bank_order_changes_only_rounding(pb, monkeypatch):
+    """The plan's bank-aware entry order permutes entries inside segments:
+    at a fixed iteration count on a well-conditioned instance, draws with and
+    without it agree to rounding (double-float and float32 products)."""
+    P = well_conditioned()
+    X, a = device_problem(P)
+    for prec, tol in (("df32", 1e-11), ("fp32", 1e-5)):
+        outs = []
+        for flag in ("1", "0"):
+            monkeypatch.setenv("PCG_BETA_BANK_PERMUTE", flag)
+            ctx = pb.Context(precision=prec, reliable_k=0)
+            r = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"],
+                                 tol=0.0, max_iter=20)
+            outs.append(r.beta.cpu().numpy())
+        assert rel(outs[0], outs[1]) < tol, prec
