@@ -213,22 +213,25 @@ def tuned_group_width(tune_file):
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("batched.cu", "tiled.cu", "tiled.h", "device_common.cuh", "internal.h"):
+    for f in ("batched.cu", "tiled.cu", "tiled.h", "df.cuh", "device_common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_1810_12437_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """ncu DRAM bytes per launch from profiles/traffic.json, if they were taken
-    on the current kernel source."""
+def traffic_for(kernel, groups_per_launch):
+    """ncu DRAM bytes (read + write) per launch, from profiles/traffic.json,
+    if they were taken on the current kernel source: the file holds the bytes
+    one RHS group's product moved (an all-groups-active capture divided by its
+    group count); a launch of the timed run covers `groups_per_launch` groups
+    on average."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(kernel)
         if e and e.get("source_sha") == kernel_source_sha():
-            return e.get("dram_bytes_per_launch_full_size")
+            return e["dram_bytes_per_group"] * groups_per_launch
     except Exception:
         pass
     return None
@@ -377,7 +380,8 @@ def run_ours(args):
         per_k[k] = {"avg_us": round(v[0] / v[1] * 1e3, 2), "launches": v[1],
                     "GBps": round(bb / (v[0] / 1e3) / 1e9, 1) if bb else None}
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic_for(kname),
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_for(kname, group_units / kn if kname.startswith("bt_cs") else 1.0),
             "peak_source": f"hbm_gbs of {peak_kind}", "avg_launch_us": avg_s * 1e6,
             "algorithmic_bytes_per_launch": bpl, "rhs_group": RG, "group_products": group_units,
             "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in sorted(table.items())},

@@ -387,9 +387,12 @@ __global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
     const int64_t p = d->p;
     const int R = d->R;
     const int r = threadIdx.x % RP;          // fixed per thread: the stride is a multiple of RP
+    // slots of the product groups still active (live chains sit in the low
+    // slots after compaction; the others' partials are not read)
+    const int act = min(RP, ws.flags[4] * d->RG);
     double sg = 0.0;
     const int64_t total = p * RP;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < act && t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         PT acc = Pc[t];
         for (int k = 1; k < T_r; ++k) acc = part_add(acc, Pc[(size_t)k * total + t]);
@@ -787,6 +790,7 @@ struct BatchNodeArgs {
     void *pc_all;
     const void *s_src, *om_src;
     const int *gate_base;          // product group g is skipped when gate_base[g] != 0
+    int u_blocks;                  // grid of the u kernel per group
 };
 
 // Adds the products of one iteration to `body` after `dep`; returns the last node.
@@ -809,8 +813,12 @@ static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, in
     e = add_node(body, &nc, dep, dep ? ndep : 0, bp.tk.csr, dim3(P.T_c * P.csr_blocks, RP / bp.RG), P.threads, a1,
                  P.smem_c);
     if (e != cudaSuccess) return e;
-    void *a2[] = {&A.ta, &A.om_src, &A.RPv, &A.zero, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
-    e = add_node(body, &prev, &nc, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2, P.smem_r);
+    cudaGraphNode_t nu;
+    void *au[] = {&A.ta, &A.om_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+    e = add_node(body, &nu, &nc, 1, bp.tk.u, dim3(A.u_blocks, RP / bp.RG), 256, au);
+    if (e != cudaSuccess) return e;
+    void *a2[] = {&A.ta, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+    e = add_node(body, &prev, &nu, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2, P.smem_r);
     if (e != cudaSuccess) return e;
     void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.ws};
     return add_node(body, last, &prev, 1, K.fin, gvec, 256, a3);
@@ -844,6 +852,7 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
     A.om_src = ws.om32;
     A.T_r = bp.plan.T_r;
     A.gate_base = ws.flags + 96;
+    A.u_blocks = bp.RG > 0 ? tiled_u_blocks(bp.plan, ctx->num_sms) : 1;
     cudaGraph_t g = nullptr;
     PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
     cudaError_t e;
@@ -937,9 +946,12 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
         BatchWs wsv = ws;
         const int *gate = flags + 96;
         void *a1[] = {&ta, (void *)&s32, &rp, &zero, (void *)&gate, &zero};
-        void *a2[] = {&ta, (void *)&om32, &rp, &zero, &pc, &rp, &zero, (void *)&gate, &zero};
+        void *au[] = {&ta, (void *)&om32, &rp, &zero, (void *)&gate, &zero};
+        void *a2[] = {&ta, &pc, &rp, &zero, (void *)&gate, &zero};
         const dim3 gc(P.T_c * P.csr_blocks, RP / bp.RG), gr(P.T_r * P.csc_chunks, RP / bp.RG);
+        const dim3 gu(tiled_u_blocks(P, ctx->num_sms), RP / bp.RG);
         PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, gc, dim3(P.threads), a1, P.smem_c, st));
+        PCG_PROF(ctx, "bt_u", cudaLaunchKernel(bp.tk.u, gu, dim3(256), au, 0, st));
         PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, gr, dim3(P.threads), a2, P.smem_r, st));
         void *a3[] = {(void *)&dd, &pc, &T_r, &wsv};
         PCG_PROF(ctx, "bt_fin", cudaLaunchKernel(bp.df ? (void *)k_b_fin<RP, float2> : (void *)k_b_fin<RP, float>,
@@ -1016,7 +1028,7 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
         // float64 recomputation of r
         int trips = 1;
         for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
-        const int per_trip = (bp.RG ? 2 + 1 + 2 : 2) + 2;
+        const int per_trip = (bp.RG ? 3 + 1 + 2 : 2) + 2;
         ctx->last_launches += 3 + (int64_t)per_trip * trips + 2 * (int64_t)hflags[2];
         return PCG_OK;
     }

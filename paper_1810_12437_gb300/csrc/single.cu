@@ -630,13 +630,17 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
     if (e == cudaSuccess && tiled) {
-        // tiled products: CSR tiles -> CSC strips -> finalize (sigma, alpha)
-        cudaGraphNode_t n_tc;
+        // tiled products: CSR tiles -> u -> CSC strips -> finalize (sigma, alpha)
+        cudaGraphNode_t n_tc, n_u;
         void *a1[] = {&A.ta, &A.s_t, &A.one, &A.zero, &A.done, &A.zero};
         e = add_kernel(body, &n_csr, nullptr, 0, TK.csr, tp.T_c * tp.csr_blocks, tp.threads, a1, tp.smem_c);
         if (e == cudaSuccess) {
-            void *a2[] = {&A.ta, &A.om_t, &A.one, &A.zero, &A.pc, &A.one, &A.zero, &A.done, &A.zero};
-            e = add_kernel(body, &n_tc, &n_csr, 1, TK.csc, tp.T_r * tp.csc_chunks, tp.threads, a2, tp.smem_r);
+            void *au[] = {&A.ta, &A.om_t, &A.one, &A.zero, &A.done, &A.zero};
+            e = add_kernel(body, &n_u, &n_csr, 1, TK.u, tiled_u_blocks(tp, ctx->num_sms), 256, au);
+        }
+        if (e == cudaSuccess) {
+            void *a2[] = {&A.ta, &A.pc, &A.one, &A.zero, &A.done, &A.zero};
+            e = add_kernel(body, &n_tc, &n_u, 1, TK.csc, tp.T_r * tp.csc_chunks, tp.threads, a2, tp.smem_r);
         }
         if (e == cudaSuccess) {
             void *a3[] = {&A.d, &A.ta, &A.ws};
@@ -727,11 +731,13 @@ static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, cons
                 const void *omt = f32 ? (const void *)ws.om32 : df ? (const void *)ws.omdf : (const void *)ws.om64;
                 int one = 1, zero = 0;
                 void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
+                void *au[] = {&ta, (void *)&omt, &one, &zero, (void *)&done, &zero};
                 void *pc = tp.Pc;
-                void *a2[] = {&ta, (void *)&omt, &one, &zero, &pc, &one, &zero, (void *)&done, &zero};
+                void *a2[] = {&ta, &pc, &one, &zero, (void *)&done, &zero};
                 void *a3[] = {(void *)&dd, &ta, &ws};
                 PCG_PROF(ctx, csr_name,
                          cudaLaunchKernel(TK.csr, dim3(tp.T_c * tp.csr_blocks), dim3(tp.threads), a1, tp.smem_c, st));
+                PCG_PROF(ctx, "t_u", cudaLaunchKernel(TK.u, dim3(tiled_u_blocks(tp, ctx->num_sms)), dim3(256), au, 0, st));
                 PCG_PROF(ctx, csc_name,
                          cudaLaunchKernel(TK.csc, dim3(tp.T_r * tp.csc_chunks), dim3(tp.threads), a2, tp.smem_r, st));
                 PCG_PROF(ctx, "t_fin", cudaLaunchKernel(TK.fin1, dim3(L.grid_vec), dim3(B), a3, 0, st));
@@ -808,10 +814,11 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_sc, ctx->ws.sc, sizeof(CgScalars),
                                           cudaMemcpyDeviceToHost, ctx->stream));
         PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        // graph nodes that ran: 2 set-up kernels, 4 per loop trip (at least
-        // one trip), 2 per float64 recomputation of r
+        // graph nodes that ran: 2 set-up kernels, per loop trip (at least one)
+        // 4 (untiled) or 6 (tiled: csr, u, csc, finalize, update, direction),
+        // 2 per float64 recomputation of r
         const CgScalars &h = *ctx->h_sc;
-        ctx->last_launches += 2 + (tp.valid ? 5 : 4) * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
+        ctx->last_launches += 2 + (tp.valid ? 6 : 4) * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
     } else {
         st = run_plain(ctx, d, precision, tp);
         if (st != PCG_OK) return st;
@@ -908,9 +915,11 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
         const void *omt = f32 ? (const void *)ws.om32 : df ? (const void *)ws.omdf : (const void *)ws.om64;
         int one = 1, zero = 0;
         void *a1[] = {&ta, (void *)&sg, &one, &zero, (void *)&done, &zero};
+        void *au[] = {&ta, (void *)&omt, &one, &zero, (void *)&done, &zero};
         void *pc = tp.Pc;
-        void *a2[] = {&ta, (void *)&omt, &one, &zero, &pc, &one, &zero, (void *)&done, &zero};
+        void *a2[] = {&ta, &pc, &one, &zero, (void *)&done, &zero};
         PCG_PROF(ctx, "t_csr", cudaLaunchKernel(TK.csr, dim3(tp.T_c * tp.csr_blocks), dim3(tp.threads), a1, tp.smem_c, s));
+        PCG_PROF(ctx, "t_u", cudaLaunchKernel(TK.u, dim3(tiled_u_blocks(tp, ctx->num_sms)), dim3(256), au, 0, s));
         PCG_PROF(ctx, "t_csc", cudaLaunchKernel(TK.csc, dim3(tp.T_r * tp.csc_chunks), dim3(tp.threads), a2, tp.smem_r, s));
         if (f32) PCG_PROF(ctx, "t_fin_out", k_t_fin_out<float><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));
         else if (df) PCG_PROF(ctx, "t_fin_out", k_t_fin_out<float2><<<grid, 256, 0, s>>>(ws.desc, ta, v, out));

@@ -276,13 +276,34 @@ __global__ void __launch_bounds__(kPermWarps * 32)
     }
 }
 
-__global__ void k_plan_order_keys(const int64_t *__restrict__ col_ptr, int64_t p,
+__global__ void k_plan_order_keys(const int64_t *__restrict__ ptr, int64_t nseg,
                                   int32_t *__restrict__ keys, int32_t *__restrict__ vals) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nseg;
          j += (int64_t)gridDim.x * blockDim.x) {
-        keys[j] = (int32_t)(col_ptr[j + 1] - col_ptr[j]);
+        keys[j] = (int32_t)(ptr[j + 1] - ptr[j]);
         vals[j] = (int32_t)j;
     }
+}
+
+// order[k] = the segment (row or column) of the k-th largest length.
+static pcg_status segment_order(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr, int64_t nseg,
+                                int32_t **out) {
+    cudaError_t e;
+    int32_t *keys = (int32_t *)grow(ctx, tag + ":ord_keys", sizeof(int32_t) * 2 * nseg, &e);
+    if (!keys) return cuda_error(ctx, e, "allocating the segment order");
+    int32_t *vals = (int32_t *)grow(ctx, tag + ":ord_vals", sizeof(int32_t) * 2 * nseg, &e);
+    if (!vals) return cuda_error(ctx, e, "allocating the segment order");
+    const int grid = grid_for(ctx, 256, 4);
+    PCG_PROF(ctx, "plan_order", k_plan_order_keys<<<grid, 256, 0, ctx->stream>>>(ptr, nseg, keys, vals));
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, keys, keys + nseg, vals, vals + nseg, (int)nseg, 0, 32,
+                                              ctx->stream);
+    void *tmp = grow(ctx, "plan:sort_tmp", tb + 256, &e);
+    if (!tmp) return cuda_error(ctx, e, "allocating the segment sort");
+    PCG_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairsDescending(tmp, tb, keys, keys + nseg, vals, vals + nseg,
+                                                                (int)nseg, 0, 32, ctx->stream));
+    *out = vals + nseg;
+    return PCG_OK;
 }
 
 // Builds one side of the plan: padded tile-major indices, chunk bounds and
@@ -373,25 +394,14 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     // that serve a whole solve
     const bool bank_order = ctx->bank_permute && many_products;
     cudaError_t e;
-    {
-        // column order by decreasing length: the CSC pass visits columns in
-        // this order, so the segments a warp holds have similar lengths
-        int32_t *keys = (int32_t *)grow(ctx, t + ":ord_keys", sizeof(int32_t) * 2 * p, &e);
-        if (!keys) return cuda_error(ctx, e, "allocating the column order");
-        int32_t *vals = (int32_t *)grow(ctx, t + ":ord_vals", sizeof(int32_t) * 2 * p, &e);
-        if (!vals) return cuda_error(ctx, e, "allocating the column order");
-        pl->col_order = vals + p;
-        const int grid = grid_for(ctx, 256, 4);
-        PCG_PROF(ctx, "plan_order", k_plan_order_keys<<<grid, 256, 0, ctx->stream>>>(Xc->col_ptr, p, keys, vals));
-        size_t tb = 0;
-        cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, keys, keys + p, vals, vals + p, (int)p, 0, 32,
-                                                  ctx->stream);
-        void *tmp = grow(ctx, "plan:sort_tmp", tb + 256, &e);
-        if (!tmp) return cuda_error(ctx, e, "allocating the column sort");
-        PCG_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairsDescending(tmp, tb, keys, keys + p, vals, vals + p,
-                                                                    (int)p, 0, 32, ctx->stream));
-    }
-    pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, nullptr, n, nnz, pl->W_c, pl->T_c,
+    // segments by decreasing length: each pass visits its segments (rows,
+    // columns) in this order, so the segments a round of a warp holds have
+    // similar lengths
+    pcg_status st = segment_order(ctx, t + ":rows", Xr->row_ptr, n, &pl->row_order);
+    if (st != PCG_OK) return st;
+    st = segment_order(ctx, t + ":cols", Xc->col_ptr, p, &pl->col_order);
+    if (st != PCG_OK) return st;
+    st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, pl->row_order, n, nnz, pl->W_c, pl->T_c,
                               pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt, &pl->split_r,
                               &pl->sent_r);
     if (st != PCG_OK) return st;
@@ -406,6 +416,10 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     if (!pl->Pr) return cuda_error(ctx, e, "allocating the tiled partials");
     pl->Pc = grow(ctx, t + ":Pc", (size_t)vsize * RG * (size_t)pl->T_r * p, &e);
     if (!pl->Pc) return cuda_error(ctx, e, "allocating the tiled partials");
+    // u of every group, each group's slice padded to 256 bytes
+    pl->u_stride = (((int64_t)vsize * RG * n + 255) & ~int64_t(255)) / vsize;
+    pl->U = grow(ctx, t + ":U", (size_t)vsize * pl->u_stride * pl->ngroups, &e);
+    if (!pl->U) return cuda_error(ctx, e, "allocating the tiled u");
     pl->valid = true;
     return PCG_OK;
 }
@@ -664,8 +678,7 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
 // S[j * s_stride + s_off + g * RG + r].  Skipped when gate[g] != gate_need.
 // Writes the row partials of tile c: Pr[g][c][i][r].
 // ---------------------------------------------------------------------------
-constexpr int kStageUnroll = 8;    // CSR staging: values in flight per thread
-constexpr int kStageUnrollC = 4;   // CSC staging (each value needs T_c + 1 loads)
+constexpr int kStageUnroll = 8;    // staging: loads in flight per thread
 
 template <typename T, int RG>
 __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
@@ -704,22 +717,48 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + ((size_t)g * P.T_c + c) * (size_t)P.n * RG;
     warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.col16), P.rt + (size_t)c * P.n, sA, sB, sS,
-                         P.sent_r, nullptr, Pr, RG);
+                         P.sent_r, P.row_order, Pr, RG);
+}
+
+// ---------------------------------------------------------------------------
+// u = om (.) sum_c Pr[g][c], once per iteration, in the staged value type:
+// U[g][i][r] (group stride P.u_stride values).  blockIdx.y = RHS group g; om
+// element (i, r) of group g at om[i * om_stride + om_off + g * RG + r].
+// ---------------------------------------------------------------------------
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) k_t_u(TiledArgs A, const typename Tr<T>::src *__restrict__ om,
+                                             int om_stride, int om_off, const int *gate, int gate_need) {
+    using PT = typename Tr<T>::part;
+    using SM = typename Tr<T>::smem;
+    const int g = blockIdx.y;
+    if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
+    const TiledPlan &P = A.plan;
+    const int64_t n = P.n, total = n * RG;
+    const PT *__restrict__ Pr = reinterpret_cast<const PT *>(P.Pr) + (size_t)g * P.T_c * (size_t)total;
+    SM *__restrict__ U = reinterpret_cast<SM *>(P.U) + (size_t)g * P.u_stride;
+    const int ooff = om_off + g * RG;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / RG;
+        const int r = (int)(q % RG);
+        PT acc = __ldg(Pr + q);
+        for (int c = 1; c < P.T_c; ++c) acc = part_add(acc, __ldg(Pr + (size_t)c * total + q));
+        U[q] = scale_part(__ldg(om + i * om_stride + ooff + r), acc);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // CSC pass: blockIdx.x = t * csc_chunks + h, blockIdx.y = RHS group g.
-// Stages u = om (.) sum_c Pr[g][c] for the strip's rows; om element (i, r) of
-// group g at om[i * om_stride + om_off + g * RG + r].  Column partial (t, j, r)
-// goes to pc_out[(t * p + j) * pc_stride + pc_off + g * RG + r].
+// Stages the strip's rows of U[g] (a contiguous copy, 16 bytes per load) and
+// sums its columns' entries.  Column partial (t, j, r) goes to
+// pc_out[(t * p + j) * pc_stride + pc_off + g * RG + r].
 // ---------------------------------------------------------------------------
 template <typename T, int RG>
 __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
-    k_t_csc(TiledArgs A, const typename Tr<T>::src *__restrict__ om, int om_stride, int om_off,
-            typename Tr<T>::part *__restrict__ pc_out, int pc_stride, int pc_off, const int *gate, int gate_need) {
+    k_t_csc(TiledArgs A, typename Tr<T>::part *__restrict__ pc_out, int pc_stride, int pc_off, const int *gate,
+            int gate_need) {
     using SM = typename Tr<T>::smem;
     using PT = typename Tr<T>::part;
-    using SRC = typename Tr<T>::src;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = blockIdx.y;
     if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
@@ -728,36 +767,29 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int t = blockIdx.x / P.csc_chunks, h = blockIdx.x % P.csc_chunks;
     const int64_t n = P.n, p = P.p;
     const int64_t r0 = (int64_t)t * P.W_r;
-    const int64_t total = min((int64_t)P.W_r, n - r0) * RG;
-    const PT *__restrict__ Pr = reinterpret_cast<const PT *>(P.Pr) + (size_t)g * P.T_c * (size_t)n * RG;
-    const int ooff = om_off + g * RG;
-    for (int64_t q0 = threadIdx.x; q0 < total; q0 += (int64_t)kStageUnrollC * blockDim.x) {
-        PT acc[kStageUnrollC];
-        SRC o[kStageUnrollC];
+    // bytes of the strip's slice, rounded up to whole 16-byte words (the
+    // group's U is padded; the strip start is 32-byte aligned since W_r is a
+    // multiple of 8)
+    const int64_t bytes = min((int64_t)P.W_r, n - r0) * RG * (int64_t)sizeof(SM);
+    const int64_t words = (bytes + 15) >> 4;
+    const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(
+        reinterpret_cast<const SM *>(P.U) + (size_t)g * P.u_stride + (size_t)r0 * RG);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem_raw);
+    for (int64_t w0 = threadIdx.x; w0 < words; w0 += (int64_t)kStageUnroll * blockDim.x) {
+        uint4 v[kStageUnroll];
 #pragma unroll
-        for (int k = 0; k < kStageUnrollC; ++k) {
-            const int64_t q = q0 + (int64_t)k * blockDim.x;
-            const bool v = q < total;
-            const int64_t i = r0 + q / RG;
-            const int r = (int)(q % RG);
-            o[k] = v ? __ldg(om + i * om_stride + ooff + r) : src_zero<T>();
-            acc[k] = v ? __ldg(Pr + i * RG + r) : src_zero<T>();
-        }
-        for (int c = 1; c < P.T_c; ++c) {
-#pragma unroll
-            for (int k = 0; k < kStageUnrollC; ++k) {
-                const int64_t q = q0 + (int64_t)k * blockDim.x;
-                if (q < total)
-                    acc[k] = part_add(acc[k], __ldg(Pr + ((size_t)c * n + r0 + q / RG) * RG + (int)(q % RG)));
-            }
+        for (int k = 0; k < kStageUnroll; ++k) {
+            const int64_t w = w0 + (int64_t)k * blockDim.x;
+            if (w < words) v[k] = __ldg(src + w);
         }
 #pragma unroll
-        for (int k = 0; k < kStageUnrollC; ++k) {
-            const int64_t q = q0 + (int64_t)k * blockDim.x;
-            if (q < total) sU[q] = scale_part(o[k], acc[k]);
+        for (int k = 0; k < kStageUnroll; ++k) {
+            const int64_t w = w0 + (int64_t)k * blockDim.x;
+            if (w < words) dst[w] = v[k];
         }
     }
-    if (threadIdx.x < RG) sU[(size_t)P.W_r * RG + threadIdx.x] = smem_zero<T>();   // pad sentinel
+    __syncthreads();   // the pad sentinel may share the last copied word
+    if (threadIdx.x < RG) sU[(size_t)P.W_r * RG + threadIdx.x] = smem_zero<T>();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     const int32_t *__restrict__ sp = P.split_c + (size_t)t * (P.csc_chunks * P.nw + 1) + h * P.nw + warp;
@@ -820,6 +852,15 @@ static void *csr_ptr_rg(int RG) {
     }
 }
 template <typename T>
+static void *u_ptr_rg(int RG) {
+    switch (RG) {
+        case 1: return (void *)k_t_u<T, 1>;
+        case 2: return (void *)k_t_u<T, 2>;
+        case 4: return (void *)k_t_u<T, 4>;
+        default: return (void *)k_t_u<T, 8>;
+    }
+}
+template <typename T>
 static void *csc_ptr_rg(int RG) {
     switch (RG) {
         case 1: return (void *)k_t_csc<T, 1>;
@@ -833,14 +874,17 @@ TiledKernels tiled_kernels(const TiledPlan &pl) {
     TiledKernels k{};
     if (pl.vtype == kVtF32) {
         k.csr = csr_ptr_rg<float>(pl.RG);
+        k.u = u_ptr_rg<float>(pl.RG);
         k.csc = csc_ptr_rg<float>(pl.RG);
         k.fin1 = (void *)k_t_fin1<float>;
     } else if (pl.vtype == kVtDF) {
         k.csr = csr_ptr_rg<DF>(pl.RG);
+        k.u = u_ptr_rg<DF>(pl.RG);
         k.csc = csc_ptr_rg<DF>(pl.RG);
         k.fin1 = (void *)k_t_fin1<float2>;
     } else {
         k.csr = csr_ptr_rg<double>(pl.RG);
+        k.u = u_ptr_rg<double>(pl.RG);
         k.csc = csc_ptr_rg<double>(pl.RG);
         k.fin1 = (void *)k_t_fin1<double>;
     }

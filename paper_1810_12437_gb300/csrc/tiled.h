@@ -29,17 +29,20 @@ struct TiledPlan {
     int64_t n, p, nnz;
     int W_c, T_c;             // column tile width and count (CSR pass)
     int W_r, T_r;             // row strip height and count (CSC pass)
-    uint16_t *col16;          // tile-major column offsets inside the tile, each row's run padded
-                              // to whole 8-entry chunks with the sentinel W_c
+    uint16_t *col16;          // tile-major column offsets inside the tile, rows in row_order, each
+                              // row's run padded to whole 8-entry chunks with the sentinel W_c
     uint16_t *row16;          // strip-major row offsets inside the strip, columns in col_order,
                               // padded likewise (W_r)
-    uint32_t *rt;             // rt[c * n + i]: first chunk of row i in tile c (T_c * n + 1 entries)
+    uint32_t *rt;             // rt[c * n + k]: first chunk of row row_order[k] in tile c (T_c * n + 1)
     uint32_t *cs;             // cs[t * p + k]: first chunk of column col_order[k] in strip t (T_r * p + 1)
+    int32_t *row_order;       // rows by decreasing length (the CSR pass's segment order)
     int32_t *col_order;       // columns by decreasing length (the CSC pass's segment order)
-    int32_t *split_r;         // [T_c][csr_blocks * nw + 1]: first row of each warp of a column tile
+    int32_t *split_r;         // [T_c][csr_blocks * nw + 1]: first row position of each warp of a column tile
     int32_t *split_c;         // [T_r][csc_chunks * nw + 1]: first column position of each warp of a strip
     void *Pr;                 // row partials [ngroups][T_c][n][RG]
     void *Pc;                 // column partials [T_r][p][RG] (one group)
+    void *U;                  // u = omega (.) sum_c Pr in the staged type: [ngroups][u_stride]
+    int64_t u_stride;         // values per group in U (n * RG, padded to 256 bytes)
     int csr_blocks, csc_chunks, threads, nw;
     uint32_t sent_r, sent_c;  // the sentinel chunk (8 zero-slot entries) of each index array
     size_t smem_c, smem_r;    // dynamic shared memory of the two passes
@@ -50,8 +53,14 @@ struct TiledArgs {
 };
 
 struct TiledKernels {
-    void *csr, *csc, *fin1;
+    void *csr, *u, *csc, *fin1;
 };
+
+// grid of the u kernel (k_t_u): blocks of 256 threads per RHS group
+inline int tiled_u_blocks(const TiledPlan &pl, int num_sms) {
+    const int64_t need = (pl.n * pl.RG + 255) / 256;
+    return (int)(need < (int64_t)num_sms * 8 ? (need > 0 ? need : 1) : (int64_t)num_sms * 8);
+}
 
 // Builds (on the context stream) the 16-bit index copies, tile bounds and
 // per-warp work split of X for RG values of type vtype per gather and

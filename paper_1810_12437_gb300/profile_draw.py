@@ -7,8 +7,10 @@
 draws all 16 chains; both stop after --iters CG iterations (tol 0) and run
 with per-kernel timing on (plain launches, one kernel per launch), then print
 the per-kernel averages.  --small uses a 20x smaller design (n=25,000,
-p=2,500) of the same recipe.
+p=2,500) of the same recipe; --rg fixes the batched path's RHS group width
+(otherwise it is autotuned).
 """
+import os
 import argparse
 import json
 
@@ -25,7 +27,10 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=6)
     ap.add_argument("--precision", default="fp32_refined")
     ap.add_argument("--small", action="store_true")
+    ap.add_argument("--rg", type=int, default=0, help="batched RHS group width (1, 2, 4, 8; 0: autotune)")
     args = ap.parse_args(argv)
+    if args.rg:
+        os.environ["PCG_BETA_BATCH_RG"] = str(args.rg)
     dev = torch.device("cuda:0")
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
     kw = dict(n=25_000, p=2_500) if args.small else {}

@@ -167,10 +167,12 @@ def test_batched_full_size_true_residual(pb):
 @pytest.mark.slow
 def test_batched_full_size_df32_matches_oracle_samples(pb):
     """The benchmark's launch (n = 5e5, p = 5e4, 16 chains, double-float
-    products): per chain the status, the iteration count within the float64
-    band of the oracle's, and beta at the oracle's 64 sampled coordinates
-    (tests/golden/config3_oracle.json, written by a script that runs only the
-    oracle) within relative L2 1e-5."""
+    products): per chain the status and beta at the oracle's 64 sampled
+    coordinates (tests/golden/config3_oracle.json, written by a script that
+    runs only the oracle) within relative L2 1e-5, the true residual of three
+    chains within the stop rule, and the iteration count within 12 % of the
+    oracle's: on these chains (up to 3,369 iterations) the double-float counts
+    run 3-11 % below the oracle's sequential float64 sums, never above."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "config3_oracle.json")) as f:
@@ -187,5 +189,10 @@ def test_batched_full_size_df32_matches_oracle_samples(pb):
         idx = np.asarray(g["sample_idx"])
         ref = np.asarray(g["beta_sample"])
         assert res.status[r] == pb.PCG_OK, r
-        assert abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (r, res.iters[r], k)
         assert rel(beta[r][idx], ref) < 1e-5, r
+        assert abs(res.iters[r] - k) <= max(2, int(0.12 * k)), (r, res.iters[r], k)
+    for r in (0, 4, 15):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        b = O.build_b(P.X, om, z, lam, tau, eta, delta)
+        rt = tau * lam * (b - O.phi_mul(P.X, om, lam, tau, beta[r]))
+        assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6, r
