@@ -168,18 +168,22 @@ def tile_geometry(n, p, RG, vsize=4):
 
 
 def bytes_per_launch(kernel, n, p, nnz, RP, RG=1):
-    """Algorithmic bytes of one launch: every stored index read once (2 bytes,
-    pad slots not counted), chunk bounds, every gathered vector read once (it
-    is staged on chip), every output written once.  Values are 4 bytes in the
-    float32 kernels and 8 bytes in the double-float ones (pairs of floats
-    staged, float64 partial sums)."""
+    """Algorithmic bytes of one launch (per RHS group for the tiled kernels):
+    every stored index read once (2 bytes, pad slots not counted), chunk
+    bounds and segment orders once, every gathered vector read once (it is
+    staged on chip), every output written once.  Values are 4 bytes in the
+    float32 kernels and 8 bytes in the double-float ones (pairs of floats)."""
     vs = 8 if kernel.endswith("df32") else 4
     if kernel in ("bt_csr_f32", "t_csr_f32", "bt_csr_df32", "t_csr_df32"):
         Tc, _ = tile_geometry(n, p, RG, vs)
-        return 2 * nnz + 4 * (Tc * n + 1) + vs * RG * p + vs * RG * Tc * n
+        return 2 * nnz + 4 * (Tc * n + 1) + 4 * n + vs * RG * (p + Tc * n)
+    if kernel in ("bt_u", "t_u"):
+        Tc, _ = tile_geometry(n, p, RG, 8 if "df32" in PRECISION else 4)
+        v = 8 if "df32" in PRECISION else 4
+        return v * RG * (Tc * n + n + n)
     if kernel in ("bt_csc_f32", "t_csc_f32", "bt_csc_df32", "t_csc_df32"):
-        Tc, Tr = tile_geometry(n, p, RG, vs)
-        return 2 * nnz + 4 * (Tr * p + 1) + 4 * p + vs * RG * (Tc * n + n) + vs * RG * Tr * p
+        _, Tr = tile_geometry(n, p, RG, vs)
+        return 2 * nnz + 4 * (Tr * p + 1) + 4 * p + vs * RG * (n + Tr * p)
     if kernel == "bt_fin":
         return None
     if kernel == "b_csr_f32":
@@ -364,7 +368,7 @@ def run_ours(args):
         bb = bytes_per_launch(k, P.X.n, P.X.p, P.X.nnz, RP, RG)
         if bb is None:
             return None
-        return bb * (group_units if k.startswith("bt_cs") else launches)
+        return bb * (group_units if k.startswith(("bt_cs", "bt_u")) else launches)
 
     top = max(table.items(), key=lambda kv: kv[1][0])
     kname, (kms, kn) = top
@@ -381,7 +385,7 @@ def run_ours(args):
                     "GBps": round(bb / (v[0] / 1e3) / 1e9, 1) if bb else None}
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_for(kname, group_units / kn if kname.startswith("bt_cs") else 1.0),
+            "traffic": traffic_for(kname, group_units / kn if kname.startswith(("bt_cs", "bt_u")) else 1.0),
             "peak_source": f"hbm_gbs of {peak_kind}", "avg_launch_us": avg_s * 1e6,
             "algorithmic_bytes_per_launch": bpl, "rhs_group": RG, "group_products": group_units,
             "kernel_shares": {k: round(v[0] / total_ms, 4) for k, v in sorted(table.items())},
