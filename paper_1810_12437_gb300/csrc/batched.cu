@@ -394,8 +394,7 @@ __global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
     const int64_t total = p * RP;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < act && t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        PT acc = Pc[t];
-        for (int k = 1; k < T_r; ++k) acc = part_add(acc, Pc[(size_t)k * total + t]);
+        const PT acc = sum_strided(Pc + t, T_r, (size_t)total);
         const double s = ws.s64[t];
         const double v = part_to_double(acc) + ws.dg[t] * s;
         ws.v64[t] = v;

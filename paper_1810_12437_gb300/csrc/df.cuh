@@ -44,6 +44,17 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
     return df_norm(p, e);
 }
 
+// Two independent TwoSums on packed pairs (sm_100 FADD2 / FFMA2: one
+// instruction per two lanes of work); x - y is formed as fma(y, -1, x), whose
+// product is exact, so it rounds exactly as the subtraction.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &t, float2 &e) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    t = __fadd2_rn(a, b);
+    const float2 bv = __ffma2_rn(a, m1, t);    // t - a
+    const float2 tb = __ffma2_rn(bv, m1, t);   // t - bv
+    e = __fadd2_rn(__ffma2_rn(tb, m1, a), __ffma2_rn(bv, m1, b));   // (a - tb) + (b - bv)
+}
+
 // generic helpers over the partial-sum types of the tiled products
 __device__ __forceinline__ float part_add(float a, float b) { return a + b; }
 __device__ __forceinline__ double part_add(double a, double b) { return a + b; }
@@ -51,5 +62,21 @@ __device__ __forceinline__ float2 part_add(float2 a, float2 b) { return df_add(a
 __device__ __forceinline__ double part_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double part_to_double(double a) { return a; }
 __device__ __forceinline__ double part_to_double(float2 a) { return df_to_double(a); }
+
+// sum_{k < K} x[k * stride] in the fixed order ((x0 + x1) + (x2 + x3)) + ... per block
+// of four, the four loads of a block issued together (K is a runtime count of
+// tile or strip partials)
+template <typename PT>
+__device__ __forceinline__ PT sum_strided(const PT *__restrict__ x, int K, size_t stride) {
+    PT acc = __ldg(x);
+    int k = 1;
+    for (; k + 4 <= K; k += 4) {
+        const PT a = __ldg(x + (size_t)k * stride), b = __ldg(x + (size_t)(k + 1) * stride);
+        const PT c = __ldg(x + (size_t)(k + 2) * stride), d = __ldg(x + (size_t)(k + 3) * stride);
+        acc = part_add(acc, part_add(part_add(a, b), part_add(c, d)));
+    }
+    for (; k < K; ++k) acc = part_add(acc, __ldg(x + (size_t)k * stride));
+    return acc;
+}
 
 }  // namespace pcg

@@ -77,8 +77,7 @@ __global__ void k_t_fin_out(const DrawDesc *__restrict__ d, TiledArgs A, const d
     const T *__restrict__ Pc = reinterpret_cast<const T *>(P.Pc);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
-        T acc = Pc[j];
-        for (int t = 1; t < P.T_r; ++t) acc = part_add(acc, Pc[(size_t)t * p + j]);
+        const T acc = sum_strided(Pc + j, P.T_r, (size_t)p);
         out[j] = part_to_double(acc) + prior_prec(d->tau, d->lambda[j]) * v[j];
     }
 }

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include <cub/cub.cuh>
 
@@ -467,7 +468,8 @@ __device__ __forceinline__ double scale_part(double o, double a) { return o * a;
 __device__ __forceinline__ float2 scale_part(float2 o, float2 a) { return df_mul(o, a); }
 
 // Accumulators of RG sums, in two independent sets (entries alternate between
-// them, so consecutive additions do not wait on each other).
+// them, so consecutive additions do not wait on each other).  Even RG sums
+// run as packed pairs (FADD2).
 template <typename T, int RG>
 struct Vec {
     T v[2][RG];
@@ -483,21 +485,28 @@ struct Vec {
 #pragma unroll
             for (int r = 0; r < RG; r += 4) {
                 const float4 x = *reinterpret_cast<const float4 *>(base + r);
-                v[K][r] += x.x; v[K][r + 1] += x.y; v[K][r + 2] += x.z; v[K][r + 3] += x.w;
+                add2<K>(r, make_float2(x.x, x.y));
+                add2<K>(r + 2, make_float2(x.z, x.w));
             }
         } else if constexpr (sizeof(T) == 4 && RG == 2) {
-            const float2 x = *reinterpret_cast<const float2 *>(base);
-            v[K][0] += x.x; v[K][1] += x.y;
+            add2<K>(0, *reinterpret_cast<const float2 *>(base));
         } else if constexpr (sizeof(T) == 8 && RG % 2 == 0) {
 #pragma unroll
             for (int r = 0; r < RG; r += 2) {
                 const double2 x = *reinterpret_cast<const double2 *>(base + r);
-                v[K][r] += x.x; v[K][r + 1] += x.y;
+                v[K][r] += x.x;
+                v[K][r + 1] += x.y;
             }
         } else {
 #pragma unroll
             for (int r = 0; r < RG; ++r) v[K][r] += base[r];
         }
+    }
+    template <int K>
+    __device__ __forceinline__ void add2(int r, float2 x) {   // float only: v[K][r..r+1] += x
+        const float2 s = __fadd2_rn(make_float2(v[K][r], v[K][r + 1]), x);
+        v[K][r] = s.x;
+        v[K][r + 1] = s.y;
     }
     // merges the two sets, then sums over aligned groups of 2^lg lanes
     // (every lane of the warp calls it)
@@ -512,37 +521,50 @@ struct Vec {
     __device__ __forceinline__ T out(int r) const { return v[0][r]; }
 };
 
+// Double-float sums.  A staged row holds RG values as [hi_0 .. hi_{RG-1},
+// lo_0 .. lo_{RG-1}] (for RG = 1 simply (hi, lo)), so that for even RG the his
+// and los of two right-hand sides are adjacent pairs and their TwoSums run
+// packed (two_sum2).  s: running sums, c: their accumulated rounding errors.
 template <int RG>
 struct Vec<DF, RG> {
-    float s[2][RG], c[2][RG];   // running sums and their accumulated rounding errors
+    static constexpr int NP = RG >= 2 ? RG / 2 : 1;   // packed pairs (RG = 1: scalar)
+    float2 s[2][NP], c[2][NP];
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
-            for (int r = 0; r < RG; ++r) s[k][r] = c[k][r] = 0.f;
-    }
-    template <int K>
-    __device__ __forceinline__ void add1(int r, float2 x) {
-        float t, e;
-        two_sum(s[K][r], x.x, t, e);
-        s[K][r] = t;
-        c[K][r] += e + x.y;
+            for (int q = 0; q < NP; ++q) s[k][q] = c[k][q] = make_float2(0.f, 0.f);
     }
     template <int K>
     __device__ __forceinline__ void add_smem(const float2 *base) {
-        if constexpr (RG % 2 == 0) {
-#pragma unroll
-            for (int r = 0; r < RG; r += 2) {
-                const float4 x = *reinterpret_cast<const float4 *>(base + r);
-                add1<K>(r, make_float2(x.x, x.y));
-                add1<K>(r + 1, make_float2(x.z, x.w));
-            }
+        const float *f = reinterpret_cast<const float *>(base);
+        if constexpr (RG == 1) {
+            const float2 x = *reinterpret_cast<const float2 *>(f);
+            float t, e;
+            two_sum(s[K][0].x, x.x, t, e);
+            s[K][0].x = t;
+            c[K][0].x += e + x.y;
+        } else if constexpr (RG == 2) {
+            const float4 x = *reinterpret_cast<const float4 *>(f);   // hi0 hi1 lo0 lo1
+            add_pair<K>(0, make_float2(x.x, x.y), make_float2(x.z, x.w));
         } else {
 #pragma unroll
-            for (int r = 0; r < RG; ++r) add1<K>(r, base[r]);
+            for (int q = 0; q < NP; q += 2) {
+                const float4 h = *reinterpret_cast<const float4 *>(f + 2 * q);
+                const float4 l = *reinterpret_cast<const float4 *>(f + RG + 2 * q);
+                add_pair<K>(q, make_float2(h.x, h.y), make_float2(l.x, l.y));
+                add_pair<K>(q + 1, make_float2(h.z, h.w), make_float2(l.z, l.w));
+            }
         }
     }
-    __device__ __forceinline__ void merge2(float &s0, float &c0, float s1, float c1) {
+    template <int K>
+    __device__ __forceinline__ void add_pair(int q, float2 hi, float2 lo) {
+        float2 t, e;
+        two_sum2(s[K][q], hi, t, e);
+        s[K][q] = t;
+        c[K][q] = __fadd2_rn(c[K][q], __fadd2_rn(e, lo));
+    }
+    __device__ __forceinline__ static void merge2(float &s0, float &c0, float s1, float c1) {
         float t, e;
         two_sum(s0, s1, t, e);
         s0 = t;
@@ -550,17 +572,40 @@ struct Vec<DF, RG> {
     }
     __device__ __forceinline__ void reduce(int lg) {
 #pragma unroll
-        for (int r = 0; r < RG; ++r) merge2(s[0][r], c[0][r], s[1][r], c[1][r]);
+        for (int q = 0; q < NP; ++q) {
+            merge2(s[0][q].x, c[0][q].x, s[1][q].x, c[1][q].x);
+            if (RG >= 2) merge2(s[0][q].y, c[0][q].y, s[1][q].y, c[1][q].y);
+        }
         for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
 #pragma unroll
-            for (int r = 0; r < RG; ++r) {
-                const float os = __shfl_xor_sync(kFull, s[0][r], o), oc = __shfl_xor_sync(kFull, c[0][r], o);
-                merge2(s[0][r], c[0][r], os, oc);
+            for (int q = 0; q < NP; ++q) {
+                float os = __shfl_xor_sync(kFull, s[0][q].x, o), oc = __shfl_xor_sync(kFull, c[0][q].x, o);
+                merge2(s[0][q].x, c[0][q].x, os, oc);
+                if (RG >= 2) {
+                    os = __shfl_xor_sync(kFull, s[0][q].y, o);
+                    oc = __shfl_xor_sync(kFull, c[0][q].y, o);
+                    merge2(s[0][q].y, c[0][q].y, os, oc);
+                }
             }
         }
     }
-    __device__ __forceinline__ float2 out(int r) const { return df_norm(s[0][r], c[0][r]); }
+    __device__ __forceinline__ float2 out(int r) const {
+        const float2 sq = s[0][r >> 1], cq = c[0][r >> 1];
+        return (r & 1) ? df_norm(sq.y, cq.y) : df_norm(sq.x, cq.x);
+    }
 };
+
+// Writes value r of a staged row (the split layout above for double-float).
+template <typename T, int RG>
+__device__ __forceinline__ void store_staged(typename Tr<T>::smem *row, int r, typename Tr<T>::smem v) {
+    if constexpr (std::is_same<T, DF>::value) {
+        float *f = reinterpret_cast<float *>(row);
+        f[r] = v.x;
+        f[RG + r] = v.y;
+    } else {
+        row[r] = v;
+    }
+}
 
 // Adds the gathered values of one whole chunk of 8 indices (pad slots point
 // at the zero sentinel, so every entry is added unconditionally).
@@ -707,7 +752,7 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
 #pragma unroll
         for (int k = 0; k < kStageUnroll; ++k) {
             const int64_t t = t0 + (int64_t)k * blockDim.x;
-            if (t < total) sS[t] = v[k];
+            if (t < total) store_staged<T, RG>(sS + (t / RG) * RG, (int)(t % RG), v[k]);
         }
     }
     if (threadIdx.x < RG) sS[(size_t)P.W_c * RG + threadIdx.x] = smem_zero<T>();   // pad sentinel
@@ -741,9 +786,8 @@ __global__ void __launch_bounds__(256) k_t_u(TiledArgs A, const typename Tr<T>::
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q / RG;
         const int r = (int)(q % RG);
-        PT acc = __ldg(Pr + q);
-        for (int c = 1; c < P.T_c; ++c) acc = part_add(acc, __ldg(Pr + (size_t)c * total + q));
-        U[q] = scale_part(__ldg(om + i * om_stride + ooff + r), acc);
+        const PT acc = sum_strided(Pr + q, P.T_c, (size_t)total);
+        store_staged<T, RG>(U + i * RG, r, scale_part(__ldg(om + i * om_stride + ooff + r), acc));
     }
 }
 
@@ -815,8 +859,7 @@ __global__ void __launch_bounds__(256) k_t_fin1(const DrawDesc *__restrict__ d, 
     double sig = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
-        T acc = Pc[j];
-        for (int t = 1; t < P.T_r; ++t) acc = part_add(acc, Pc[(size_t)t * p + j]);
+        const T acc = sum_strided(Pc + j, P.T_r, (size_t)p);
         const double sj = ws.s64[j];
         const double v = part_to_double(acc) + prior_prec(tau, d->lambda[j]) * sj;
         ws.v64[j] = v;
