@@ -59,6 +59,18 @@ struct BatchWs {
     BatchDesc *desc;
 };
 
+// Slots a per-element kernel must visit: those of the product groups still
+// active (live chains sit in the low slots after compaction), rounded up to a
+// power of two a2 <= RP so that a thread keeps one slot (threadIdx.x mod a2)
+// and the rest of the grid covers the elements.  All RP slots before any
+// compaction or in the untiled layout.
+__device__ __forceinline__ int active_slots_pow2(const BatchDesc *__restrict__ d, const int *flags, int RP) {
+    const int act = d->RG > 0 ? min(RP, flags[4] * d->RG) : RP;
+    int a2 = 1;
+    while (a2 < act) a2 <<= 1;
+    return a2;
+}
+
 // Grid reduction of NV values per block held in shared memory (vals), summed
 // in a fixed order.  Returns true in the last block, where sums[] holds the
 // totals.
@@ -386,24 +398,24 @@ __global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
     if (*(volatile const int *)&ws.flags[0]) return;
     const int64_t p = d->p;
     const int R = d->R;
-    const int r = threadIdx.x % RP;          // fixed per thread: the stride is a multiple of RP
-    // slots of the product groups still active (live chains sit in the low
-    // slots after compaction; the others' partials are not read)
-    const int act = min(RP, ws.flags[4] * d->RG);
+    // only the slots of active product groups (the others' partials are not read)
+    const int a2 = active_slots_pow2(d, ws.flags, RP);
+    const int lg2 = __ffs(a2) - 1;
+    const int r = threadIdx.x & (a2 - 1);    // fixed per thread: the stride is a multiple of a2
     double sg = 0.0;
     const int64_t total = p * RP;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < act && t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (p << lg2);
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = (q >> lg2) * RP + r;
         const PT acc = sum_strided(Pc + t, T_r, (size_t)total);
         const double s = ws.s64[t];
         const double v = part_to_double(acc) + ws.dg[t] * s;
         ws.v64[t] = v;
         sg += s * v;
     }
-#pragma unroll
-    for (int o = 16; o >= RP; o >>= 1) sg += __shfl_xor_sync(kFull, sg, o);
+    for (int o = 16; o >= a2; o >>= 1) sg += __shfl_xor_sync(kFull, sg, o);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (lane < RP) part[wib][lane] = sg;
+    if (lane < RP) part[wib][lane] = lane < a2 ? sg : 0.0;
     __syncthreads();
     if (threadIdx.x < RP) {
         double a = 0.0;
@@ -444,14 +456,16 @@ __global__ void __launch_bounds__(256) k_b_update(const BatchDesc *__restrict__ 
     }
     const int64_t p = d->p;
     const int R = d->R;
-    const int r = threadIdx.x % RP;          // fixed per thread: the stride is a multiple of RP
+    const int a2 = active_slots_pow2(d, ws.flags, RP);
+    const int lg2 = __ffs(a2) - 1;
+    const int r = threadIdx.x & (a2 - 1);    // fixed per thread: the stride is a multiple of a2
     const bool live = r < R && !ws.sc[r].done;
     const double alpha = live ? ws.sc[r].alpha : 0.0;
     double rho = 0.0;
-    const int64_t total = p * RP;
     if (live) {
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-             t += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (p << lg2);
+             q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t t = (q >> lg2) * RP + r;
             const double bj = ws.beta[t] + alpha * ws.s64[t];
             const double rj = ws.r[t] - alpha * ws.v64[t];
             ws.beta[t] = bj;
@@ -459,11 +473,10 @@ __global__ void __launch_bounds__(256) k_b_update(const BatchDesc *__restrict__ 
             rho += rj * (ws.m[t] * rj);
         }
     }
-    // lanes with equal r: xor over the lane bits above RP
-#pragma unroll
-    for (int o = 16; o >= RP; o >>= 1) rho += __shfl_xor_sync(kFull, rho, o);
+    // lanes with equal r: xor over the lane bits above a2
+    for (int o = 16; o >= a2; o >>= 1) rho += __shfl_xor_sync(kFull, rho, o);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (RP <= 32 && lane < RP) part[wib][lane] = rho;
+    if (RP <= 32 && lane < RP) part[wib][lane] = lane < a2 ? rho : 0.0;
     __syncthreads();
     if (threadIdx.x < RP) {
         double a = 0.0;
@@ -611,13 +624,15 @@ __global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d,
     const int all = *(volatile const int *)&ws.flags[0];
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_while, all ? 0u : 1u);
     if (all) return;
-    const int r = threadIdx.x % RP;
+    const int a2 = active_slots_pow2(d, ws.flags, RP);
+    const int lg2 = __ffs(a2) - 1;
+    const int r = threadIdx.x & (a2 - 1);    // fixed per thread: the stride is a multiple of a2
     if (r >= d->R || ws.sc[r].done) return;
     const double gamma = ws.sc[r].gamma;
-    const int64_t total = d->p * RP;
     const bool df = d->df != 0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (d->p << lg2);
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = (q >> lg2) * RP + r;
         const double s = ws.m[t] * ws.r[t] + gamma * ws.s64[t];
         ws.s64[t] = s;
         if (df) reinterpret_cast<float2 *>(ws.s32)[t] = df_from_double(s);
