@@ -42,15 +42,12 @@ namespace pcg {
 // ---------------------------------------------------------------------------
 
 // bounds[t * nseg + s] = first position in segment s whose index is >= t * W,
-// for t = 0..T (t = 0 gives the segment start, t = T its end).  Segment s is
-// the stored segment order[s] when an order is given.
-__global__ void k_plan_bounds(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                              const int32_t *__restrict__ order, int64_t nseg, int W, int T,
-                              uint32_t *__restrict__ bounds) {
+// for t = 0..T (t = 0 gives the segment start, t = T its end).
+__global__ void k_plan_bounds(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                              int W, int T, uint32_t *__restrict__ bounds) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = order ? (int64_t)order[s] : s;
-        const int64_t a = ptr[o], b = ptr[o + 1];
+        const int64_t a = ptr[s], b = ptr[s + 1];
         bounds[s] = (uint32_t)a;
         int64_t lo = a;
         for (int t = 1; t < T; ++t) {
@@ -68,35 +65,49 @@ __global__ void k_plan_bounds(const int64_t *__restrict__ ptr, const int32_t *__
     }
 }
 
-// chunks[t * nseg + s] = number of 8-index chunks of segment s in tile t
-// (its entries rounded up to a multiple of 8); chunks[T * nseg] = 0.
-__global__ void k_plan_chunks(const uint32_t *__restrict__ bounds, int64_t nseg, int T,
-                              uint32_t *__restrict__ chunks) {
+// Sort keys of the per-tile segment order: tile ascending, then chunk count
+// descending (key = t << 32 | ~chunks), value = the segment.
+__global__ void k_plan_tile_keys(const uint32_t *__restrict__ bounds, int64_t nseg, int T,
+                                 uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    const int64_t total = (int64_t)T * nseg;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = q / nseg, s = q - t * nseg;
+        const uint32_t ch = (bounds[(t + 1) * nseg + s] - bounds[t * nseg + s] + 7u) >> 3;
+        keys[q] = ((uint64_t)t << 32) | (uint64_t)(~ch);
+        vals[q] = (int32_t)s;
+    }
+}
+
+// chunks[t * nseg + k] = number of 8-index chunks (entries rounded up to a
+// multiple of 8) of segment order[t * nseg + k] in tile t; chunks[T * nseg] = 0.
+__global__ void k_plan_chunks_sorted(const uint32_t *__restrict__ bounds, const int32_t *__restrict__ order,
+                                     int64_t nseg, int T, uint32_t *__restrict__ chunks) {
     const int64_t total = (int64_t)T * nseg;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q <= total;
          q += (int64_t)gridDim.x * blockDim.x) {
         if (q == total) {
             chunks[q] = 0u;
         } else {
-            const int64_t t = q / nseg, s = q - t * nseg;
-            const uint32_t len = bounds[(t + 1) * nseg + s] - bounds[t * nseg + s];
-            chunks[q] = (len + 7u) >> 3;
+            const int64_t t = q / nseg, s = order[q];
+            chunks[q] = (bounds[(t + 1) * nseg + s] - bounds[t * nseg + s] + 7u) >> 3;
         }
     }
 }
 
-// Writes each (tile t, segment s) run of indices, as offsets inside the tile,
-// to its own whole chunks starting at chunk cstart[t * nseg + s]; the slots
-// after the run are filled with the sentinel W (a zero slot in shared memory).
-__global__ void k_plan_fill(const int32_t *__restrict__ idx, const uint32_t *__restrict__ bounds,
-                            const uint32_t *__restrict__ cstart, int64_t nseg, int T, int W,
-                            uint16_t *__restrict__ out) {
+// Writes the run of indices of the k-th segment of tile t (segment
+// order[t * nseg + k]), as offsets inside the tile, to its own whole chunks
+// starting at chunk cstart[t * nseg + k]; the slots after the run are filled
+// with the sentinel W (a zero slot in shared memory).
+__global__ void k_plan_fill_sorted(const int32_t *__restrict__ idx, const uint32_t *__restrict__ bounds,
+                                   const int32_t *__restrict__ order, const uint32_t *__restrict__ cstart,
+                                   int64_t nseg, int T, int W, uint16_t *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = (int64_t)T * nseg;
     for (int64_t q = warp; q < total; q += nwarps) {
-        const int64_t t = q / nseg, s = q - t * nseg;
+        const int64_t t = q / nseg, s = order[q];
         const uint32_t a = bounds[t * nseg + s], b = bounds[(t + 1) * nseg + s];
         const uint32_t len = b - a, padded = (len + 7u) & ~7u;
         const uint64_t dst = (uint64_t)cstart[q] * 8u;
@@ -277,67 +288,53 @@ __global__ void __launch_bounds__(kPermWarps * 32)
     }
 }
 
-__global__ void k_plan_order_keys(const int64_t *__restrict__ ptr, int64_t nseg,
-                                  int32_t *__restrict__ keys, int32_t *__restrict__ vals) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nseg;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        keys[j] = (int32_t)(ptr[j + 1] - ptr[j]);
-        vals[j] = (int32_t)j;
-    }
-}
-
-// order[k] = the segment (row or column) of the k-th largest length.
-static pcg_status segment_order(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr, int64_t nseg,
-                                int32_t **out) {
-    cudaError_t e;
-    int32_t *keys = (int32_t *)grow(ctx, tag + ":ord_keys", sizeof(int32_t) * 2 * nseg, &e);
-    if (!keys) return cuda_error(ctx, e, "allocating the segment order");
-    int32_t *vals = (int32_t *)grow(ctx, tag + ":ord_vals", sizeof(int32_t) * 2 * nseg, &e);
-    if (!vals) return cuda_error(ctx, e, "allocating the segment order");
-    const int grid = grid_for(ctx, 256, 4);
-    PCG_PROF(ctx, "plan_order", k_plan_order_keys<<<grid, 256, 0, ctx->stream>>>(ptr, nseg, keys, vals));
-    size_t tb = 0;
-    cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, keys, keys + nseg, vals, vals + nseg, (int)nseg, 0, 32,
-                                              ctx->stream);
-    void *tmp = grow(ctx, "plan:sort_tmp", tb + 256, &e);
-    if (!tmp) return cuda_error(ctx, e, "allocating the segment sort");
-    PCG_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairsDescending(tmp, tb, keys, keys + nseg, vals, vals + nseg,
-                                                                (int)nseg, 0, 32, ctx->stream));
-    *out = vals + nseg;
-    return PCG_OK;
-}
-
 // Builds one side of the plan: padded tile-major indices, chunk bounds and
 // the per-warp work split.
 static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr,
-                            const int32_t *idx, const int32_t *order, int64_t nseg, int64_t nnz, int W,
-                            int T, int nwt, int value_bytes, bool bank_order, uint16_t **out_idx,
-                            uint32_t **out_cb, int32_t **out_split, uint32_t *out_sent) {
+                            const int32_t *idx, int64_t nseg, int64_t nnz, int W, int T, int nwt,
+                            int value_bytes, bool bank_order, uint16_t **out_idx, uint32_t **out_cb,
+                            int32_t **out_split, uint32_t *out_sent, int32_t **out_keys) {
     cudaError_t e;
     const int64_t nb = (int64_t)(T + 1) * nseg;
+    const int64_t nts = (int64_t)T * nseg;
     uint32_t *bounds = (uint32_t *)grow(ctx, tag + ":bounds", sizeof(uint32_t) * nb, &e);
     if (!bounds) return cuda_error(ctx, e, "allocating the tiled plan");
-    const int64_t nc = (int64_t)T * nseg + 1;
+    const int64_t nc = nts + 1;
     uint32_t *chunks = (uint32_t *)grow(ctx, tag + ":chunks", sizeof(uint32_t) * nc, &e);
     if (!chunks) return cuda_error(ctx, e, "allocating the tiled plan");
     uint32_t *cb = (uint32_t *)grow(ctx, tag + ":cb", sizeof(uint32_t) * nc, &e);
     if (!cb) return cuda_error(ctx, e, "allocating the tiled plan");
     int32_t *split = (int32_t *)grow(ctx, tag + ":split", sizeof(int32_t) * (size_t)T * (nwt + 1), &e);
     if (!split) return cuda_error(ctx, e, "allocating the tiled plan");
+    uint64_t *skeys = (uint64_t *)grow(ctx, tag + ":sort_keys", sizeof(uint64_t) * 2 * nts, &e);
+    if (!skeys) return cuda_error(ctx, e, "allocating the tiled plan");
+    int32_t *svals = (int32_t *)grow(ctx, tag + ":sort_vals", sizeof(int32_t) * 2 * nts, &e);
+    if (!svals) return cuda_error(ctx, e, "allocating the tiled plan");
     // at most 7 pad slots per segment, then the sentinel chunk
-    const int64_t cap = ((nnz + 7 * (int64_t)T * nseg + 7) & ~int64_t(7)) + 8;
+    const int64_t cap = ((nnz + 7 * nts + 7) & ~int64_t(7)) + 8;
     uint16_t *pidx = (uint16_t *)grow(ctx, tag + ":idx", sizeof(uint16_t) * cap, &e);
     if (!pidx) return cuda_error(ctx, e, "allocating the tiled plan");
-    size_t tmp_bytes = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, chunks, cb, (int)nc, ctx->stream);
-    void *tmp = grow(ctx, "plan:scan_tmp", tmp_bytes + 256, &e);
-    if (!tmp) return cuda_error(ctx, e, "allocating the plan scan");
+    size_t scan_bytes = 0, sort_bytes = 0;
+    int tbits = 1;
+    while ((1 << tbits) < T) ++tbits;
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, chunks, cb, (int)nc, ctx->stream);
+    cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, skeys, skeys + nts, svals, svals + nts, (int)nts, 0,
+                                    32 + tbits, ctx->stream);
+    void *tmp = grow(ctx, "plan:tmp", std::max(scan_bytes, sort_bytes) + 256, &e);
+    if (!tmp) return cuda_error(ctx, e, "allocating the plan scratch");
     const int grid = grid_for(ctx, 256, 8);
     cudaStream_t s = ctx->stream;
-    PCG_PROF(ctx, "plan_bounds", k_plan_bounds<<<grid, 256, 0, s>>>(ptr, idx, order, nseg, W, T, bounds));
-    PCG_PROF(ctx, "plan_chunks", k_plan_chunks<<<grid, 256, 0, s>>>(bounds, nseg, T, chunks));
-    PCG_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, chunks, cb, (int)nc, s));
-    PCG_PROF(ctx, "plan_fill", k_plan_fill<<<grid, 256, 0, s>>>(idx, bounds, cb, nseg, T, W, pidx));
+    int32_t *order = svals + nts;
+    // segment bounds per tile in the stored order, then every tile's segments
+    // by decreasing chunk count (stable: ties keep the stored order), so the
+    // segments a round of a warp holds have nearly equal lengths
+    PCG_PROF(ctx, "plan_bounds", k_plan_bounds<<<grid, 256, 0, s>>>(ptr, idx, nseg, W, T, bounds));
+    PCG_PROF(ctx, "plan_order", k_plan_tile_keys<<<grid, 256, 0, s>>>(bounds, nseg, T, skeys, svals));
+    PCG_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairs(tmp, sort_bytes, skeys, skeys + nts, svals, order, (int)nts,
+                                                      0, 32 + tbits, s));
+    PCG_PROF(ctx, "plan_chunks", k_plan_chunks_sorted<<<grid, 256, 0, s>>>(bounds, order, nseg, T, chunks));
+    PCG_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, scan_bytes, chunks, cb, (int)nc, s));
+    PCG_PROF(ctx, "plan_fill", k_plan_fill_sorted<<<grid, 256, 0, s>>>(idx, bounds, order, cb, nseg, T, W, pidx));
     const uint32_t sent = (uint32_t)(cap / 8 - 1);
     k_plan_sentinel<<<1, 32, 0, s>>>(pidx + (size_t)sent * 8, W);
     PCG_PROF(ctx, "plan_split", k_plan_split<<<grid_for(ctx, 256, 1), 256, 0, s>>>(cb, nseg, T, nwt, split));
@@ -353,6 +350,7 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
     *out_cb = cb;
     *out_split = split;
     *out_sent = sent;
+    *out_keys = order;
     return PCG_OK;
 }
 
@@ -395,20 +393,12 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     // that serve a whole solve
     const bool bank_order = ctx->bank_permute && many_products;
     cudaError_t e;
-    // segments by decreasing length: each pass visits its segments (rows,
-    // columns) in this order, so the segments a round of a warp holds have
-    // similar lengths
-    pcg_status st = segment_order(ctx, t + ":rows", Xr->row_ptr, n, &pl->row_order);
+    pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, n, nnz, pl->W_c, pl->T_c,
+                              pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt,
+                              &pl->split_r, &pl->sent_r, &pl->row_keys);
     if (st != PCG_OK) return st;
-    st = segment_order(ctx, t + ":cols", Xc->col_ptr, p, &pl->col_order);
-    if (st != PCG_OK) return st;
-    st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, pl->row_order, n, nnz, pl->W_c, pl->T_c,
-                              pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt, &pl->split_r,
-                              &pl->sent_r);
-    if (st != PCG_OK) return st;
-    st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, pl->col_order, p, nnz, pl->W_r, pl->T_r,
-                   pl->csc_chunks * pl->nw, RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c,
-                   &pl->sent_c);
+    st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, p, nnz, pl->W_r, pl->T_r, pl->csc_chunks * pl->nw,
+                   RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c, &pl->sent_c, &pl->col_keys);
     if (st != PCG_OK) return st;
     // partial sums: float for float values, double otherwise (DF included);
     // row partials per group, column partials of one group (callers with
@@ -762,7 +752,7 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + ((size_t)g * P.T_c + c) * (size_t)P.n * RG;
     warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.col16), P.rt + (size_t)c * P.n, sA, sB, sS,
-                         P.sent_r, P.row_order, Pr, RG);
+                         P.sent_r, P.row_keys + (size_t)c * P.n, Pr, RG);
 }
 
 // ---------------------------------------------------------------------------
@@ -840,7 +830,7 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pc = pc_out + (size_t)t * p * pc_stride + pc_off + g * RG;
     warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.row16), P.cs + (size_t)t * p, sA, sB, sU,
-                         P.sent_c, P.col_order, Pc, pc_stride);
+                         P.sent_c, P.col_keys + (size_t)t * p, Pc, pc_stride);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,14 +29,15 @@ struct TiledPlan {
     int64_t n, p, nnz;
     int W_c, T_c;             // column tile width and count (CSR pass)
     int W_r, T_r;             // row strip height and count (CSC pass)
-    uint16_t *col16;          // tile-major column offsets inside the tile, rows in row_order, each
-                              // row's run padded to whole 8-entry chunks with the sentinel W_c
-    uint16_t *row16;          // strip-major row offsets inside the strip, columns in col_order,
-                              // padded likewise (W_r)
-    uint32_t *rt;             // rt[c * n + k]: first chunk of row row_order[k] in tile c (T_c * n + 1)
-    uint32_t *cs;             // cs[t * p + k]: first chunk of column col_order[k] in strip t (T_r * p + 1)
-    int32_t *row_order;       // rows by decreasing length (the CSR pass's segment order)
-    int32_t *col_order;       // columns by decreasing length (the CSC pass's segment order)
+    uint16_t *col16;          // tile-major column offsets inside the tile, each tile's rows by
+                              // decreasing length in the tile (row_keys), each row's run padded to
+                              // whole 8-entry chunks with the sentinel W_c
+    uint16_t *row16;          // strip-major row offsets inside the strip, each strip's columns by
+                              // decreasing length in the strip (col_keys), padded likewise (W_r)
+    uint32_t *rt;             // rt[c * n + k]: first chunk of row row_keys[c * n + k] in tile c (T_c * n + 1)
+    uint32_t *cs;             // cs[t * p + k]: first chunk of column col_keys[t * p + k] in strip t (T_r * p + 1)
+    int32_t *row_keys;        // [T_c][n]: the rows of each tile in the CSR pass's segment order
+    int32_t *col_keys;        // [T_r][p]: the columns of each strip in the CSC pass's segment order
     int32_t *split_r;         // [T_c][csr_blocks * nw + 1]: first row position of each warp of a column tile
     int32_t *split_c;         // [T_r][csc_chunks * nw + 1]: first column position of each warp of a strip
     void *Pr;                 // row partials [ngroups][T_c][n][RG]
