@@ -93,7 +93,7 @@ typedef struct pcg_csc {
 } pcg_csc;
 
 typedef struct pcg_options {
-    int precision;              /* PCG_PREC_*, default PCG_PREC_FP32_REFINED */
+    int precision;              /* PCG_PREC_*, default PCG_PREC_DF32 */
     int reliable_k;             /* refined mode: also recompute r every k iterations (0: only
                                    before stopping); default 50 */
     int stop_rule;              /* PCG_STOP_*, default PCG_STOP_PAPER_RMS */
@@ -166,6 +166,8 @@ pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
  * dense-block pass per iteration over the RHS block.  beta (out): nrhs*p,
  * chain-major.  iters, resid, status (host, nrhs each) receive each chain's
  * result; the return value is the worst status.  1 <= nrhs <= 32.
+ * Precisions PCG_PREC_DF32, PCG_PREC_FP32_REFINED and PCG_PREC_FP32
+ * (PCG_PREC_FP64 returns PCG_BADARG).
  */
 pcg_status pcg_draw_beta_batched(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
                                  int nrhs, const double *omega, const double *z,
@@ -188,6 +190,8 @@ typedef struct pcg_problem {
  * from a device queue; each problem advances its own CG with per-problem
  * barriers whose waits are bounded (PCG_TIMEOUT if one gives up).
  * probs: host array of nprob descriptors.  iters, resid, status: host, nprob.
+ * Its products are float64 (PCG_PREC_FP64) or float32; PCG_PREC_DF32 runs
+ * as PCG_PREC_FP32_REFINED (float32 products, float64 recomputation of r).
  */
 pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol,
                                 int max_iter, int *iters, double *resid, int *status);

@@ -176,7 +176,7 @@ class DeviceDesign:
 class Context:
     """Owns a ``pcg_ctx``: workspace, cached graphs, options and stream."""
 
-    def __init__(self, precision="fp32_refined", reliable_k=50, stop_rule="rms", use_graph=True,
+    def __init__(self, precision="df32", reliable_k=50, stop_rule="rms", use_graph=True,
                  stream: Optional[torch.cuda.Stream] = None, autotune_cache: Optional[str] = None,
                  profile: bool = False):
         lib = load_library()

@@ -209,7 +209,7 @@ extern "C" {
 
 pcg_status pcg_options_default(pcg_options *opt) {
     if (!opt) return PCG_BADARG;
-    opt->precision = PCG_PREC_FP32_REFINED;
+    opt->precision = PCG_PREC_DF32;
     opt->reliable_k = 50;
     opt->stop_rule = PCG_STOP_PAPER_RMS;
     opt->use_graph = 1;

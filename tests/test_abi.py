@@ -49,7 +49,7 @@ def test_options_default(lib):
     from paper_1810_12437_gb300._native import _Options
     o = _Options()
     assert lib.pcg_options_default(ctypes.byref(o)) == 0
-    assert (o.precision, o.reliable_k, o.stop_rule, o.use_graph) == (1, 50, 0, 1)
+    assert (o.precision, o.reliable_k, o.stop_rule, o.use_graph) == (3, 50, 0, 1)   # PCG_PREC_DF32
     assert lib.pcg_options_default(None) == 4
 
 
