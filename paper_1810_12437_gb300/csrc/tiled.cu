@@ -180,6 +180,8 @@ __device__ __forceinline__ int lanes_log2(uint32_t chunks, uint32_t nseg) {
 constexpr int kPermRounds = 4;
 constexpr int kPermWarps = 8;
 constexpr int kPermChunks = kBlk;   // chunks per lane and block: 32 entries, one bit each
+// the entry sets below are 32-bit masks (one bit per entry of a lane's block)
+static_assert(kPermChunks * 8 <= 32, "the bank-order kernel tracks a block's entries in 32-bit masks");
 
 __global__ void __launch_bounds__(kPermWarps * 32)
     k_plan_permute(uint16_t *__restrict__ idx16, const uint32_t *__restrict__ cb_all,
