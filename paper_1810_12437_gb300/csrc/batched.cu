@@ -36,12 +36,14 @@ struct BatchDesc {
     int max_iter, stop_rule, refined, reliable_k;
     int RG;   // right-hand sides per tiled product group (0: untiled products)
     int df;   // double-float products: s32 / om32 hold float pairs (float2)
+    int tail; // a group-width-1 plan takes over the products when one chain is left
 };
 
 // flags[] layout (kFlagInts ints, device):
 //   [0] all chains done, [1] some chain needs the float64 recomputation,
 //   [2] iterations that ran it, [3] a compaction was planned this iteration,
 //   [4] active product groups, [5] compactions so far,
+//   [6] 1 once the tail plan runs the products, [7] 0 while it runs (its gate),
 //   [32 + s] chain held by slot s, [64 + s] old slot moved to slot s by the compaction,
 //   [96 + g] 1 when product group g holds no live chain (its products are skipped).
 constexpr int kFlagInts = 128;
@@ -274,6 +276,8 @@ __global__ void __launch_bounds__(256) k_b_init(const BatchDesc *__restrict__ d,
             ws.flags[3] = 0;
             ws.flags[4] = d->RG > 0 ? RP / d->RG : 1;
             ws.flags[5] = 0;
+            ws.flags[6] = 0;
+            ws.flags[7] = 1;
         }
         if (threadIdx.x < 32) {
             ws.flags[96 + threadIdx.x] = 0;
@@ -390,12 +394,16 @@ __global__ void __launch_bounds__(256) k_b_csc(const BatchDesc *__restrict__ d,
 
 // Tiled products: v = sum_t Pc[t] + d s (float64), sigma per chain, alpha.
 template <int RP, typename PT>
-__global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d,
-                                               const PT *__restrict__ Pc, int T_r, BatchWs ws) {
+__global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d, const PT *__restrict__ Pc_main,
+                                               int T_main, const PT *__restrict__ Pc_tail, int T_tail,
+                                               BatchWs ws) {
     __shared__ double part[8][RP];
     __shared__ double vals[RP];
     __shared__ double sums[RP];
     if (*(volatile const int *)&ws.flags[0]) return;
+    const bool tail = ws.flags[6] != 0;
+    const PT *__restrict__ Pc = tail ? Pc_tail : Pc_main;
+    const int T_r = tail ? T_tail : T_main;
     const int64_t p = d->p;
     const int R = d->R;
     // only the slots of active product groups (the others' partials are not read)
@@ -655,7 +663,13 @@ __global__ void k_b_compact_plan(const BatchDesc *__restrict__ d, BatchWs ws) {
             int live = 0;
             for (int s = 0; s < R; ++s) live += ws.sc[s].done ? 0 : 1;
             const int need = (live + RG - 1) / RG;
-            if (need < ws.flags[4]) {
+            // one chain left: the group-width-1 plan takes over (the chain moves to slot 0)
+            const bool to_tail = d->tail && live == 1 && !ws.flags[6];
+            if (to_tail) {
+                ws.flags[6] = 1;
+                ws.flags[7] = 0;
+            }
+            if (need < ws.flags[4] || to_tail) {
                 int k = 0;
                 for (int s = 0; s < R; ++s)
                     if (!ws.sc[s].done) perm[k++] = s;
@@ -682,7 +696,7 @@ __global__ void k_b_compact_plan(const BatchDesc *__restrict__ d, BatchWs ws) {
         ws.flags[32 + s] = chain[s];
         ws.flags[64 + s] = perm[s];
     }
-    if (s < 32) ws.flags[96 + s] = (s >= ws.flags[4]) ? 1 : 0;
+    if (s < 32) ws.flags[96 + s] = (ws.flags[6] || s >= ws.flags[4]) ? 1 : 0;
 }
 
 template <int RP, typename V>
@@ -779,10 +793,15 @@ static BatchKernels kernels_for(int RP, bool df = false) {
 // RP / RG groups of RG right-hand sides.
 struct BatchProducts {
     int RG = 0;
-    bool df = false;           // double-float products (sources s64 / om64, double partials)
+    bool df = false;           // double-float products (float-pair sources and partials)
     TiledPlan plan{};
     TiledKernels tk{};
-    void *pc_all = nullptr;    // [T_r][p][RP] partials (float, or double with df)
+    void *pc_all = nullptr;    // [T_r][p][RP] partials (float, or float pairs with df)
+    // tail plan: group width 1 over slot 0, for the last live chain (RG >= 2 only)
+    bool tail = false;
+    TiledPlan plan1{};
+    TiledKernels tk1{};
+    void *pc1 = nullptr;       // [T_r1][p][RP] partials of the tail plan
 };
 
 struct BatchNodeArgs {
@@ -805,6 +824,11 @@ struct BatchNodeArgs {
     const void *s_src, *om_src;
     const int *gate_base;          // product group g is skipped when gate_base[g] != 0
     int u_blocks;                  // grid of the u kernel per group
+    // tail plan (group width 1, slot 0), gated by flags[7]
+    TiledArgs ta1;
+    void *pc1;
+    const int *gate_tail;
+    int u_blocks1, T_r1;
 };
 
 // Adds the products of one iteration to `body` after `dep`; returns the last node.
@@ -834,7 +858,22 @@ static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, in
     void *a2[] = {&A.ta, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
     e = add_node(body, &prev, &nu, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2, P.smem_r);
     if (e != cudaSuccess) return e;
-    void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.ws};
+    if (bp.tail) {
+        // the same products by the tail plan (exit at once until it takes over)
+        const TiledPlan &Q = bp.plan1;
+        cudaGraphNode_t t1, tu, t2;
+        void *b1[] = {&A.ta1, &A.s_src, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        e = add_node(body, &t1, &prev, 1, bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), Q.threads, b1, Q.smem_c);
+        if (e != cudaSuccess) return e;
+        void *bu[] = {&A.ta1, &A.om_src, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        e = add_node(body, &tu, &t1, 1, bp.tk1.u, dim3(A.u_blocks1, 1), 256, bu);
+        if (e != cudaSuccess) return e;
+        void *b2[] = {&A.ta1, &A.pc1, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        e = add_node(body, &t2, &tu, 1, bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), Q.threads, b2, Q.smem_r);
+        if (e != cudaSuccess) return e;
+        prev = t2;
+    }
+    void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.pc1, &A.T_r1, &A.ws};
     return add_node(body, last, &prev, 1, K.fin, gvec, 256, a3);
 }
 
@@ -867,6 +906,11 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
     A.T_r = bp.plan.T_r;
     A.gate_base = ws.flags + 96;
     A.u_blocks = bp.RG > 0 ? tiled_u_blocks(bp.plan, ctx->num_sms) : 1;
+    A.ta1.plan = bp.plan1;
+    A.pc1 = bp.tail ? bp.pc1 : bp.pc_all;
+    A.gate_tail = ws.flags + 7;
+    A.u_blocks1 = bp.tail ? tiled_u_blocks(bp.plan1, ctx->num_sms) : 1;
+    A.T_r1 = bp.tail ? bp.plan1.T_r : bp.plan.T_r;
     cudaGraph_t g = nullptr;
     PCG_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
     cudaError_t e;
@@ -967,7 +1011,22 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
         PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, gc, dim3(P.threads), a1, P.smem_c, st));
         PCG_PROF(ctx, "bt_u", cudaLaunchKernel(bp.tk.u, gu, dim3(256), au, 0, st));
         PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, gr, dim3(P.threads), a2, P.smem_r, st));
-        void *a3[] = {(void *)&dd, &pc, &T_r, &wsv};
+        void *pc1 = bp.tail ? bp.pc1 : bp.pc_all;
+        int T_r1 = bp.tail ? bp.plan1.T_r : P.T_r;
+        if (bp.tail) {
+            const TiledPlan &Q = bp.plan1;
+            TiledArgs ta1{Q};
+            const int *gt = flags + 7;
+            void *b1[] = {&ta1, (void *)&s32, &rp, &zero, (void *)&gt, &zero};
+            void *bu[] = {&ta1, (void *)&om32, &rp, &zero, (void *)&gt, &zero};
+            void *b2[] = {&ta1, &pc1, &rp, &zero, (void *)&gt, &zero};
+            PCG_PROF(ctx, bp.df ? "bt1_csr_df32" : "bt1_csr_f32",
+                     cudaLaunchKernel(bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), dim3(Q.threads), b1, Q.smem_c, st));
+            PCG_PROF(ctx, "bt1_u", cudaLaunchKernel(bp.tk1.u, dim3(tiled_u_blocks(Q, ctx->num_sms), 1), dim3(256), bu, 0, st));
+            PCG_PROF(ctx, bp.df ? "bt1_csc_df32" : "bt1_csc_f32",
+                     cudaLaunchKernel(bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), dim3(Q.threads), b2, Q.smem_r, st));
+        }
+        void *a3[] = {(void *)&dd, &pc, &T_r, &pc1, &T_r1, &wsv};
         PCG_PROF(ctx, "bt_fin", cudaLaunchKernel(bp.df ? (void *)k_b_fin<RP, float2> : (void *)k_b_fin<RP, float>,
                                                  dim3(gvec), dim3(256), a3, 0, st));
     }
@@ -991,7 +1050,7 @@ static void launch_batch_plain_init(pcg_ctx *ctx, const BatchWs &ws, int grid) {
 
 // Tiled products for a group width RG (0: untiled).
 static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int RP, int RG,
-                                BatchProducts *bp) {
+                                BatchProducts *bp, bool with_tail) {
     *bp = BatchProducts{};
     const bool df = ctx->opt.precision == PCG_PREC_DF32;
     if ((RG == 0 || !ctx->tiled_enabled) && !df) return PCG_OK;
@@ -1009,6 +1068,24 @@ static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *
     if (!bp->pc_all) return cuda_error(ctx, e, "allocating the batched partials");
     bp->RG = RG;
     bp->df = df;
+    // PCG_BETA_BATCH_TAIL=0 in the environment keeps the main plan to the end
+    const char *tail_env = getenv("PCG_BETA_BATCH_TAIL");
+    if (with_tail && RG >= 2 && !(tail_env && tail_env[0] == '0')) {
+        // group width 1 for the last live chain: half the staged bytes per
+        // gather of the main plan's width-RG groups
+        char tag1[32];
+        snprintf(tag1, sizeof tag1, "batchtail%s", df ? "d" : "");
+        st = build_tiled_plan(ctx, tag1, Xr, Xc, 1, df ? kVtDF : kVtF32, 1, true, &bp->plan1);
+        if (st != PCG_OK) return st;
+        if (bp->plan1.valid) {
+            st = tiled_prepare(ctx, bp->plan1, &bp->tk1);
+            if (st != PCG_OK) return st;
+            bp->pc1 = grow(ctx, std::string(tag1) + ":pc1",
+                           (df ? sizeof(double) : sizeof(float)) * (size_t)bp->plan1.T_r * bp->plan1.p * RP, &e);
+            if (!bp->pc1) return cuda_error(ctx, e, "allocating the batched partials");
+            bp->tail = true;
+        }
+    }
     return PCG_OK;
 }
 
@@ -1018,12 +1095,11 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
     cudaError_t e;
     if (ctx->opt.use_graph && !ctx->opt.profile) {
         char key[256];
-        snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p|%d%s:%d:%d:%d:%d:%d:%d:%lld:%lld:%p:%p:%p:%p:%p:%p",
-                 RP, (int)refined, grid, gvec, (void *)ws.b, ws.u, (void *)ws.om64, (void *)ws.om32, bp.RG, bp.df ? "d" : "",
-                 bp.plan.T_c, bp.plan.T_r, bp.plan.csr_blocks, bp.plan.csc_chunks,
-                 bp.plan.nw, bp.plan.threads, (long long)bp.plan.n,
-                 (long long)bp.plan.p, (void *)bp.plan.col16, (void *)bp.plan.row16, (void *)bp.plan.rt,
-                 (void *)bp.plan.cs, bp.plan.Pr, (void *)bp.pc_all);
+        snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p:%p|%d%s%s:%016llx:%016llx:%p:%p",
+                 RP, (int)refined, grid, gvec, (void *)ws.b, ws.u, (void *)ws.om64, (void *)ws.om32, (void *)ws.flags,
+                 bp.RG, bp.df ? "d" : "", bp.tail ? "t" : "",
+                 (unsigned long long)plan_fingerprint(bp.plan),
+                 (unsigned long long)(bp.tail ? plan_fingerprint(bp.plan1) : 0ull), bp.pc_all, bp.pc1);
         auto it = ctx->named_graphs.find(key);
         cudaGraphExec_t exec = nullptr;
         if (it == ctx->named_graphs.end()) {
@@ -1042,7 +1118,7 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
         // float64 recomputation of r
         int trips = 1;
         for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
-        const int per_trip = (bp.RG ? 3 + 1 + 2 : 2) + 2;
+        const int per_trip = (bp.RG ? 3 + (bp.tail ? 3 : 0) + 1 + 2 : 2) + 2;
         ctx->last_launches += 3 + (int64_t)per_trip * trips + 2 * (int64_t)hflags[2];
         return PCG_OK;
     }
@@ -1130,10 +1206,11 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
         for (int rg : cands) {
             if (rg > RP || (df && (rg == 0 || rg > 4))) continue;
             BatchProducts bp;
-            pcg_status st = make_products(ctx, Xr, Xc, RP, rg, &bp);
+            pcg_status st = make_products(ctx, Xr, Xc, RP, rg, &bp, false);
             if (st != PCG_OK) return st;
             if (rg && !bp.RG) continue;
             d.RG = bp.RG;
+            d.tail = 0;
             *hd = d;
             PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
             float ms = 0.f;
@@ -1251,10 +1328,11 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     pcg_status st = choose_rg(ctx, Xr, Xc, ws, d, hd, RP, refined, nrhs, hsc, hflags, &RG);
     if (st != PCG_OK) return st;
     BatchProducts bp;
-    st = make_products(ctx, Xr, Xc, RP, RG, &bp);
+    st = make_products(ctx, Xr, Xc, RP, RG, &bp, true);
     if (st != PCG_OK) return st;
     ctx->last_launches = 0;
     d.RG = bp.RG;
+    d.tail = bp.tail ? 1 : 0;
     *hd = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
     st = batched_once(ctx, ws, RP, refined, nrhs, max_iter, bp, hsc, hflags);

@@ -794,10 +794,9 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         // shapes (never a caller pointer: those are read from the descriptor).
         const SingleLaunch L = single_launch(ctx, d);
         char key[256];
-        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d|%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p",
+        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d|%d:%016llx",
                  L.G_row, L.G_col, L.grid_stream, L.grid_vec, precision, d.refined, mode, (int)tp.valid,
-                 tp.W_c, tp.T_c, tp.W_r, tp.T_r, tp.csr_blocks, tp.csc_chunks, tp.nw,
-                 (void *)tp.col16, (void *)tp.row16, (void *)tp.rt, (void *)tp.cs, tp.Pr, tp.Pc);
+                 (unsigned long long)(tp.valid ? plan_fingerprint(tp) : 0ull));
         // n and p enter through the plan only when it is valid
         std::string skey = std::string(key) + (tp.valid ? ":" + std::to_string(tp.n) + ":" + std::to_string(tp.p) : "");
         auto it = ctx->named_graphs.find(skey);

@@ -905,6 +905,24 @@ static void *csc_ptr_rg(int RG) {
     }
 }
 
+uint64_t plan_fingerprint(const TiledPlan &pl) {
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the fields
+    auto mix = [&](uint64_t v) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (v >> (8 * k)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    const void *ptrs[] = {pl.col16, pl.row16, pl.rt, pl.cs, pl.row_keys, pl.col_keys, pl.split_r, pl.split_c,
+                          pl.Pr, pl.Pc, pl.U};
+    for (const void *q : ptrs) mix((uint64_t)(uintptr_t)q);
+    const int64_t vals[] = {pl.valid, pl.RG, pl.vsize, pl.vtype, pl.ngroups, pl.n, pl.p, pl.nnz, pl.W_c, pl.T_c,
+                            pl.W_r, pl.T_r, pl.u_stride, pl.csr_blocks, pl.csc_chunks, pl.threads, pl.nw,
+                            pl.sent_r, pl.sent_c, (int64_t)pl.smem_c, (int64_t)pl.smem_r};
+    for (int64_t v : vals) mix((uint64_t)v);
+    return h;
+}
+
 TiledKernels tiled_kernels(const TiledPlan &pl) {
     TiledKernels k{};
     if (pl.vtype == kVtF32) {

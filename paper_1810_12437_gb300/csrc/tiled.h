@@ -72,6 +72,9 @@ inline int tiled_u_blocks(const TiledPlan &pl, int num_sms) {
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
                             int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl);
 TiledKernels tiled_kernels(const TiledPlan &pl);
+// A hash of every field of the plan (its buffers and shapes): cached graphs
+// bake the plan into their kernel parameters, so their keys include it.
+uint64_t plan_fingerprint(const TiledPlan &pl);
 // kernel pointers plus their dynamic shared-memory attributes
 pcg_status tiled_prepare(pcg_ctx *ctx, const TiledPlan &pl, TiledKernels *k);
 

@@ -137,6 +137,30 @@ def test_batched_df32_every_group_width(pb, small3, rg, monkeypatch):
         assert rel(beta[r], ref) < 1e-5, r
 
 
+def test_batched_tail_plan(pb, small3, monkeypatch):
+    """With group width 2, a group-width-1 plan takes over the products when
+    one chain is left (it gathers half the bytes per nonzero): draws with and
+    without it both match the oracle, and the tail plan's launches appear in
+    the launch count."""
+    monkeypatch.setenv("PCG_BETA_BATCH_RG", "2")
+    P = small3
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    runs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PCG_BETA_BATCH_TAIL", flag)
+        ctx = pb.Context(precision="df32")
+        res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
+        runs[flag] = (res, pb.pcg_last_kernel_launches(ctx))
+    assert runs["1"][1] > runs["0"][1]
+    for flag, (res, _) in runs.items():
+        beta = res.beta.cpu().numpy()
+        for r in range(16):
+            om, z, lam, tau, eta, delta = chain(P, r)
+            ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
+            assert res.status[r] == pb.PCG_OK and abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (flag, r)
+            assert rel(beta[r], ref) < 1e-5, (flag, r)
+
+
 def test_batched_fp64_mode_rejected(pb, small3):
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
