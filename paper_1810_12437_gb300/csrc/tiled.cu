@@ -156,8 +156,12 @@ __global__ void k_plan_split(const uint32_t *__restrict__ cb, int64_t nseg, int 
     }
 }
 
-// lanes per segment (log2) for a warp whose segments hold `chunks` chunks in all
+// lanes per segment (log2) for a warp whose segments hold `chunks` chunks in
+// all: one lane when they average at most two chunks (adjacent lanes then read
+// adjacent segments), else the fewest lanes (at least two, so that a group
+// reads whole sectors) that cover a typical segment with one block each
 __device__ __forceinline__ int lanes_log2(uint32_t chunks, uint32_t nseg) {
+    if (chunks <= 2u * nseg) return 0;
     const uint32_t mean = (chunks + nseg - 1) / nseg;
     int lg = 1;
     while (lg < 5 && ((uint32_t)kBlk << lg) < mean) ++lg;
