@@ -63,17 +63,21 @@ __device__ __forceinline__ double part_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double part_to_double(double a) { return a; }
 __device__ __forceinline__ double part_to_double(float2 a) { return df_to_double(a); }
 
-// sum_{k < K} x[k * stride] in the fixed order ((x0 + x1) + (x2 + x3)) + ... per block
-// of four, the four loads of a block issued together (K is a runtime count of
-// tile or strip partials)
+// sum_{k < K} x[k * stride] in a fixed order: x0, then blocks of eight added
+// as a tree ((x1 + x2) + (x3 + x4)) + ((x5 + x6) + (x7 + x8)), then the rest
+// one by one; the eight loads of a block are issued together (K is a runtime
+// count of tile or strip partials)
 template <typename PT>
 __device__ __forceinline__ PT sum_strided(const PT *__restrict__ x, int K, size_t stride) {
     PT acc = __ldg(x);
     int k = 1;
-    for (; k + 4 <= K; k += 4) {
-        const PT a = __ldg(x + (size_t)k * stride), b = __ldg(x + (size_t)(k + 1) * stride);
-        const PT c = __ldg(x + (size_t)(k + 2) * stride), d = __ldg(x + (size_t)(k + 3) * stride);
-        acc = part_add(acc, part_add(part_add(a, b), part_add(c, d)));
+    for (; k + 8 <= K; k += 8) {
+        PT v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + (size_t)(k + u) * stride);
+        const PT lo = part_add(part_add(v[0], v[1]), part_add(v[2], v[3]));
+        const PT hi = part_add(part_add(v[4], v[5]), part_add(v[6], v[7]));
+        acc = part_add(acc, part_add(lo, hi));
     }
     for (; k < K; ++k) acc = part_add(acc, __ldg(x + (size_t)k * stride));
     return acc;

@@ -57,10 +57,12 @@ struct TiledKernels {
     void *csr, *u, *csc, *fin1;
 };
 
-// grid of the u kernel (k_t_u): blocks of 256 threads per RHS group
+// grid of the u kernel (k_t_u, a grid-stride loop): blocks of 256 threads per
+// RHS group, two per SM at most (a launch whose groups are all gated off then
+// schedules few blocks)
 inline int tiled_u_blocks(const TiledPlan &pl, int num_sms) {
     const int64_t need = (pl.n * pl.RG + 255) / 256;
-    return (int)(need < (int64_t)num_sms * 8 ? (need > 0 ? need : 1) : (int64_t)num_sms * 8);
+    return (int)(need < (int64_t)num_sms * 2 ? (need > 0 ? need : 1) : (int64_t)num_sms * 2);
 }
 
 // Builds (on the context stream) the 16-bit index copies, tile bounds and
