@@ -179,6 +179,7 @@ __device__ __forceinline__ int lanes_log2(uint32_t chunks, uint32_t nseg) {
 // distinct banks: kPermRounds rounds of proposals (each lane proposes a bank
 // it still holds, rotated per lane and slot; the lowest lane of a collision
 // wins), then the rest take any entry they hold.
+// A local search then refines that order (refine_banks).
 // nb = banks one load instruction spreads over (128 / bytes per gathered
 // value, at least 2); phase = lanes per bank phase (128 / min(bytes, 16)).
 constexpr int kPermRounds = 4;
@@ -186,10 +187,134 @@ constexpr int kPermWarps = 8;
 constexpr int kPermChunks = kBlk;   // chunks per lane and block: 32 entries, one bit each
 // the entry sets below are 32-bit masks (one bit per entry of a lane's block)
 static_assert(kPermChunks * 8 <= 32, "the bank-order kernel tracks a block's entries in 32-bit masks");
+constexpr int kRefineIters = 64;    // swap attempts per bank phase and block
+
+// Largest load of one slot's bank phase (cnt: its non-pad entries per bank;
+// z: lanes reading the zero slot, one word in bank bw however many read it)
+// and the first bank that carries it.
+__device__ __forceinline__ void slot_load(const unsigned char *cnt, int z, int nb, int bw, int &mx, int &mb) {
+    mx = 0;
+    mb = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int c = cnt[b] + (b == bw && z > 0);
+        if (c > mx) {
+            mx = c;
+            mb = b;
+        }
+    }
+}
+
+// Local search over one block's order (E[lane][slot], all 32 lanes, after the
+// greedy pass).  The cost of a slot in a bank phase is its largest number of
+// distinct words one bank serves; pad entries and lanes past their segment's
+// end all read the zero slot W, which counts as one word.  For each phase,
+// up to kRefineIters times: take a slot whose cost is above one (rotating
+// over such slots), one lane's entry in that slot's fullest bank, and let
+// every lane of the warp price the swap of that entry with the same lane's
+// entry in one other slot (lane s prices slot s); the cheapest swap is taken
+// when it does not raise the summed cost of the two slots.  A swap keeps every
+// entry in its lane's block, so the products only change in rounding.
+// scratch: 1280 bytes of this warp's shared memory.
+__device__ void refine_banks(uint16_t (*E)[kPermChunks * 8], unsigned char *scratch, uint32_t vmask, int lane,
+                             int nb, int phase, uint32_t W) {
+    const int nph = 32 / phase;
+    unsigned char *cnt = scratch;                                   // [nph][32 slots][nb]
+    unsigned char *zs = scratch + 1024;                             // [nph][32 slots]
+    uint32_t *vm = reinterpret_cast<uint32_t *>(scratch + 1152);   // per lane: valid chunks
+    __syncwarp();
+    vm[lane] = vmask;
+    const uint32_t run = __reduce_or_sync(kFull, vmask);   // chunks the warp executes
+    const int bw = (int)(W & (uint32_t)(nb - 1));
+    const int s = lane;                                     // the slot this lane counts and prices
+    const bool exe = (run >> (s >> 3)) & 1u;
+    __syncwarp();
+    for (int p = 0; p < nph; ++p) {
+        unsigned char *row = cnt + (p * 32 + s) * nb;
+        for (int b = 0; b < nb; ++b) row[b] = 0;
+        int z = 0;
+        if (exe) {
+            for (int q = 0; q < phase; ++q) {
+                const int l = p * phase + q;
+                if ((vm[l] >> (s >> 3)) & 1u) {
+                    const uint32_t x = E[l][s];
+                    if (x == W) ++z;
+                    else ++row[x & (uint32_t)(nb - 1)];
+                } else {
+                    ++z;
+                }
+            }
+        }
+        zs[p * 32 + s] = (unsigned char)z;
+    }
+    __syncwarp();
+    for (int p = 0; p < nph; ++p) {
+        for (int it = 0; it < kRefineIters; ++it) {
+            int mx = 0, mb = 0;
+            if (exe) slot_load(cnt + (p * 32 + s) * nb, zs[p * 32 + s], nb, bw, mx, mb);
+            const unsigned conf = __ballot_sync(kFull, mx >= 2);
+            if (!conf) break;
+            const int rot = (it * 13 + p * 7) & 31;
+            const int s1 = (__ffs(__funnelshift_r(conf, conf, rot)) - 1 + rot) & 31;
+            const int b1 = __shfl_sync(kFull, mb, s1);
+            const int m1 = __shfl_sync(kFull, mx, s1);
+            bool cand = false;   // lane q of the phase holds a non-pad entry of bank b1 in slot s1
+            if (lane < phase) {
+                const int l = p * phase + lane;
+                if ((vm[l] >> (s1 >> 3)) & 1u) {
+                    const uint32_t x = E[l][s1];
+                    cand = x != W && (int)(x & (uint32_t)(nb - 1)) == b1;
+                }
+            }
+            const unsigned cm = __ballot_sync(kFull, cand);
+            if (!cm) continue;
+            const int qr = (it * 5) & (phase - 1);
+            const int l = p * phase + ((__ffs(__funnelshift_r(cm, cm, qr)) - 1 + qr) & 31);
+            const uint32_t x1 = E[l][s1];
+            int delta = 1 << 16;
+            uint32_t x2 = 0;
+            int b2 = -1;
+            if (s != s1 && exe && ((vm[l] >> (s >> 3)) & 1u)) {
+                x2 = E[l][s];
+                b2 = x2 == W ? -1 : (int)(x2 & (uint32_t)(nb - 1));
+                if (b2 != b1) {
+                    const unsigned char *r1 = cnt + (p * 32 + s1) * nb, *r2 = cnt + (p * 32 + s) * nb;
+                    const int z1 = zs[p * 32 + s1] + (b2 < 0), z2 = zs[p * 32 + s] - (b2 < 0);
+                    int n1 = 0, n2 = 0;
+                    for (int b = 0; b < nb; ++b) {
+                        const int c1 = r1[b] - (b == b1) + (b == b2) + (b == bw && z1 > 0);
+                        const int c2 = r2[b] - (b == b2) + (b == b1) + (b == bw && z2 > 0);
+                        n1 = max(n1, c1);
+                        n2 = max(n2, c2);
+                    }
+                    delta = n1 + n2 - m1 - mx;
+                }
+            }
+            const unsigned key = ((unsigned)(delta + 16) << 5) | (unsigned)((s - rot) & 31);
+            const unsigned best = __reduce_min_sync(kFull, key);
+            if ((int)(best >> 5) - 16 <= 0 && key == best) {
+                unsigned char *r1 = cnt + (p * 32 + s1) * nb, *r2 = cnt + (p * 32 + s) * nb;
+                E[l][s1] = (uint16_t)x2;
+                E[l][s] = (uint16_t)x1;
+                --r1[b1];
+                ++r2[b1];
+                if (b2 < 0) {
+                    ++zs[p * 32 + s1];
+                    --zs[p * 32 + s];
+                } else {
+                    ++r1[b2];
+                    --r2[b2];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+}
 
 __global__ void __launch_bounds__(kPermWarps * 32)
     k_plan_permute(uint16_t *__restrict__ idx16, const uint32_t *__restrict__ cb_all,
-                   const int32_t *__restrict__ split, int64_t nseg, int T, int nwt, int nb, int phase) {
+                   const int32_t *__restrict__ split, int64_t nseg, int T, int nwt, int nb, int phase,
+                   uint32_t W) {
     __shared__ uint16_t ent_s[kPermWarps][32][kPermChunks * 8];
     __shared__ uint32_t bm_s[kPermWarps][32][32];   // per lane and bank: unplaced entries (bit i = ent[i])
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -279,17 +404,22 @@ __global__ void __launch_bounds__(kPermWarps * 32)
                     placed[slot] = ent[i];
                 }
             }
+            __syncwarp();   // every lane is done with its greedy pass (ent, bm)
+#pragma unroll
+            for (int i = 0; i < kPermChunks * 8; ++i) ent[i] = (vmask >> (i >> 3) & 1u) ? placed[i] : (uint16_t)W;
+            refine_banks(ent_s[wl], reinterpret_cast<unsigned char *>(bm_s[wl]), vmask, lane, nb, phase, W);
 #pragma unroll
             for (int u = 0; u < kPermChunks; ++u) {
                 if (vmask >> u & 1u) {
                     uint4 w;
-                    w.x = (uint32_t)placed[u * 8 + 0] | ((uint32_t)placed[u * 8 + 1] << 16);
-                    w.y = (uint32_t)placed[u * 8 + 2] | ((uint32_t)placed[u * 8 + 3] << 16);
-                    w.z = (uint32_t)placed[u * 8 + 4] | ((uint32_t)placed[u * 8 + 5] << 16);
-                    w.w = (uint32_t)placed[u * 8 + 6] | ((uint32_t)placed[u * 8 + 7] << 16);
+                    w.x = (uint32_t)ent[u * 8 + 0] | ((uint32_t)ent[u * 8 + 1] << 16);
+                    w.y = (uint32_t)ent[u * 8 + 2] | ((uint32_t)ent[u * 8 + 3] << 16);
+                    w.z = (uint32_t)ent[u * 8 + 4] | ((uint32_t)ent[u * 8 + 5] << 16);
+                    w.w = (uint32_t)ent[u * 8 + 6] | ((uint32_t)ent[u * 8 + 7] << 16);
                     w4[q + ((uint32_t)u << lg)] = w;
                 }
             }
+            __syncwarp();   // ent and bm are rewritten by the next block
         }
     }
 }
@@ -349,7 +479,8 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
         const int64_t sim = (int64_t)T * nwt;
         const int blocks = (int)((sim + kPermWarps - 1) / kPermWarps);
         PCG_PROF(ctx, "plan_permute",
-                 k_plan_permute<<<blocks, kPermWarps * 32, 0, s>>>(pidx, cb, split, nseg, T, nwt, nb, phase));
+                 k_plan_permute<<<blocks, kPermWarps * 32, 0, s>>>(pidx, cb, split, nseg, T, nwt, nb, phase,
+                                                                    (uint32_t)W));
     }
     PCG_CUDA_TRY(ctx, cudaGetLastError());
     *out_idx = pidx;
