@@ -9,8 +9,10 @@ right-hand sides by Eq. 2.3 and prior-preconditioned CG to the paper's RMS
 rule 1e-6 (Eq. S2), one batched launch (CUDA graph) per step.  Products in
 double-float arithmetic (pairs of floats, about 48 bits: float64-like
 iteration counts at float32 instruction rates) with float64 CG scalars and
-vectors; PCG_BENCH_PRECISION=fp32_refined selects float32 products with
-float64 reliable updates instead.
+vectors; PCG_BENCH_PRECISION=fx64 selects 64-bit fixed-point products (each
+staged tile scaled by a power of two, exact integer sums) and
+PCG_BENCH_PRECISION=fp32_refined float32 products with float64 reliable
+updates instead.
 
 Printed (rank 0, one JSON line): beta-draws/s of the whole job, the
 end-to-end rate through the public API with host buffers, the roofline of the
@@ -44,6 +46,9 @@ NRHS = 16
 TOL = 1e-6
 PRECISION = os.environ.get("PCG_BENCH_PRECISION", "df32")
 RELIABLE_K = 50
+# arithmetic of the products per precision: float pairs, 64-bit integer sums of
+# fixed-point tiles (vectors as float pairs), float64, float32
+DTYPES = {"df32": "f32x2", "fx64": "int64", "fp64": "f64"}
 WORKLOAD = ("16 chains sharing binary X, n=500000, p=50000, log10 r_j~U(-4.5,-1.5), "
             "per-chain omega~U(.05,.25), half-Cauchy lambda (2% x100), log10 tau~U(-3.5,-2.5), "
             "paper RMS stop 1e-6")
@@ -172,16 +177,18 @@ def bytes_per_launch(kernel, n, p, nnz, RP, RG=1):
     every stored index read once (2 bytes, pad slots not counted), chunk
     bounds and segment orders once, every gathered vector read once (it is
     staged on chip), every output written once.  Values are 4 bytes in the
-    float32 kernels and 8 bytes in the double-float ones (pairs of floats)."""
-    vs = 8 if kernel.endswith("df32") else 4
-    if kernel in ("bt_csr_f32", "t_csr_f32", "bt_csr_df32", "t_csr_df32"):
+    float32 kernels and 8 bytes in the double-float and fixed-point ones (pairs
+    of floats in global memory)."""
+    vs = 8 if kernel.endswith(("df32", "fx64")) else 4
+    pair = PRECISION in ("df32", "fx64")
+    if kernel in ("bt_csr_f32", "t_csr_f32", "bt_csr_df32", "t_csr_df32", "bt_csr_fx64", "t_csr_fx64"):
         Tc, _ = tile_geometry(n, p, RG, vs)
         return 2 * nnz + 4 * (Tc * n + 1) + 4 * n + vs * RG * (p + Tc * n)
     if kernel in ("bt_u", "t_u"):
-        Tc, _ = tile_geometry(n, p, RG, 8 if "df32" in PRECISION else 4)
-        v = 8 if "df32" in PRECISION else 4
+        Tc, _ = tile_geometry(n, p, RG, 8 if pair else 4)
+        v = 8 if pair else 4
         return v * RG * (Tc * n + n + n)
-    if kernel in ("bt_csc_f32", "t_csc_f32", "bt_csc_df32", "t_csc_df32"):
+    if kernel in ("bt_csc_f32", "t_csc_f32", "bt_csc_df32", "t_csc_df32", "bt_csc_fx64", "t_csc_fx64"):
         _, Tr = tile_geometry(n, p, RG, vs)
         return 2 * nnz + 4 * (Tr * p + 1) + 4 * p + vs * RG * (n + Tr * p)
     if kernel == "bt_fin":
@@ -402,7 +409,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32x2" if PRECISION == "df32" else ("f64" if PRECISION == "fp64" else "f32"), "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES.get(PRECISION, "f32"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": P.X.n, "p": P.X.p, "nnz": P.X.nnz, "nrhs": NRHS,
                    "tol": TOL, "precision": PRECISION,
                    "parallelism": f"replicas x{world} (independent chains per GPU)",

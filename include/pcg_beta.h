@@ -66,10 +66,17 @@ enum {
                                    float64; r = b - Phi beta recomputed in float64
                                    every reliable_k iterations and before stopping */
     PCG_PREC_FP32 = 2,          /* float32 products, float64 scalars, no recomputation */
-    PCG_PREC_DF32 = 3           /* double-float products: each gathered value held as a pair
+    PCG_PREC_DF32 = 3,          /* double-float products: each gathered value held as a pair
                                    of float32 (hi + lo) and summed with error-free float32
                                    TwoSum, about 48 significant bits at float32 arithmetic
                                    cost; CG scalars, beta and r in float64 */
+    PCG_PREC_FX64 = 4           /* fixed-point products: the vectors are float32 pairs as in
+                                   PCG_PREC_DF32; each tile of the gathered vector is
+                                   scaled by a power of two and rounded to 64-bit integers
+                                   (grid: about 2^-52 of the tile's largest value, with room
+                                   for the longest segment's sum), summed exactly in integer
+                                   arithmetic, and each sum converted back to a float32 pair
+                                   (the tiled products only; elsewhere as PCG_PREC_DF32) */
 };
 
 /* Stop rules.  With rho = r.(M^-1 r) = ||tau lambda (.) r||^2 (Sec. S4.2):
@@ -166,8 +173,8 @@ pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
  * dense-block pass per iteration over the RHS block.  beta (out): nrhs*p,
  * chain-major.  iters, resid, status (host, nrhs each) receive each chain's
  * result; the return value is the worst status.  1 <= nrhs <= 32.
- * Precisions PCG_PREC_DF32, PCG_PREC_FP32_REFINED and PCG_PREC_FP32
- * (PCG_PREC_FP64 returns PCG_BADARG).
+ * Precisions PCG_PREC_DF32, PCG_PREC_FX64, PCG_PREC_FP32_REFINED and
+ * PCG_PREC_FP32 (PCG_PREC_FP64 returns PCG_BADARG).
  */
 pcg_status pcg_draw_beta_batched(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
                                  int nrhs, const double *omega, const double *z,
@@ -190,8 +197,9 @@ typedef struct pcg_problem {
  * from a device queue; each problem advances its own CG with per-problem
  * barriers whose waits are bounded (PCG_TIMEOUT if one gives up).
  * probs: host array of nprob descriptors.  iters, resid, status: host, nprob.
- * Its products are float64 (PCG_PREC_FP64) or float32; PCG_PREC_DF32 runs
- * as PCG_PREC_FP32_REFINED (float32 products, float64 recomputation of r).
+ * Its products are float64 (PCG_PREC_FP64) or float32; PCG_PREC_DF32 and
+ * PCG_PREC_FX64 run as PCG_PREC_FP32_REFINED (float32 products, float64
+ * recomputation of r).
  */
 pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol,
                                 int max_iter, int *iters, double *resid, int *status);

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_pcg_beta.so")
 PCG_OK, PCG_MAXITER, PCG_BREAKDOWN, PCG_NONFINITE, PCG_BADARG, PCG_TIMEOUT, PCG_CUDA = range(7)
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN", 3: "NONFINITE", 4: "BADARG",
                 5: "TIMEOUT", 6: "CUDA"}
-PREC = {"fp64": 0, "fp32_refined": 1, "fp32": 2, "df32": 3}
+PREC = {"fp64": 0, "fp32_refined": 1, "fp32": 2, "df32": 3, "fx64": 4}
 STOP = {"rms": 0, "paper_rms": 0, "relative": 1}
 ADJ = {"solve": 0, "draw": 1}
 

@@ -793,7 +793,8 @@ static BatchKernels kernels_for(int RP, bool df = false) {
 // RP / RG groups of RG right-hand sides.
 struct BatchProducts {
     int RG = 0;
-    bool df = false;           // double-float products (float-pair sources and partials)
+    bool df = false;           // float-pair sources and partials (double-float or fixed-point products)
+    bool fx = false;           // fixed-point products
     TiledPlan plan{};
     TiledKernels tk{};
     void *pc_all = nullptr;    // [T_r][p][RP] partials (float, or float pairs with df)
@@ -1008,9 +1009,9 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
         void *a2[] = {&ta, &pc, &rp, &zero, (void *)&gate, &zero};
         const dim3 gc(P.T_c * P.csr_blocks, RP / bp.RG), gr(P.T_r * P.csc_chunks, RP / bp.RG);
         const dim3 gu(tiled_u_blocks(P, ctx->num_sms), RP / bp.RG);
-        PCG_PROF(ctx, bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, gc, dim3(P.threads), a1, P.smem_c, st));
+        PCG_PROF(ctx, bp.fx ? "bt_csr_fx64" : bp.df ? "bt_csr_df32" : "bt_csr_f32", cudaLaunchKernel(bp.tk.csr, gc, dim3(P.threads), a1, P.smem_c, st));
         PCG_PROF(ctx, "bt_u", cudaLaunchKernel(bp.tk.u, gu, dim3(256), au, 0, st));
-        PCG_PROF(ctx, bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, gr, dim3(P.threads), a2, P.smem_r, st));
+        PCG_PROF(ctx, bp.fx ? "bt_csc_fx64" : bp.df ? "bt_csc_df32" : "bt_csc_f32", cudaLaunchKernel(bp.tk.csc, gr, dim3(P.threads), a2, P.smem_r, st));
         void *pc1 = bp.tail ? bp.pc1 : bp.pc_all;
         int T_r1 = bp.tail ? bp.plan1.T_r : P.T_r;
         if (bp.tail) {
@@ -1020,10 +1021,10 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
             void *b1[] = {&ta1, (void *)&s32, &rp, &zero, (void *)&gt, &zero};
             void *bu[] = {&ta1, (void *)&om32, &rp, &zero, (void *)&gt, &zero};
             void *b2[] = {&ta1, &pc1, &rp, &zero, (void *)&gt, &zero};
-            PCG_PROF(ctx, bp.df ? "bt1_csr_df32" : "bt1_csr_f32",
+            PCG_PROF(ctx, bp.fx ? "bt1_csr_fx64" : bp.df ? "bt1_csr_df32" : "bt1_csr_f32",
                      cudaLaunchKernel(bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), dim3(Q.threads), b1, Q.smem_c, st));
             PCG_PROF(ctx, "bt1_u", cudaLaunchKernel(bp.tk1.u, dim3(tiled_u_blocks(Q, ctx->num_sms), 1), dim3(256), bu, 0, st));
-            PCG_PROF(ctx, bp.df ? "bt1_csc_df32" : "bt1_csc_f32",
+            PCG_PROF(ctx, bp.fx ? "bt1_csc_fx64" : bp.df ? "bt1_csc_df32" : "bt1_csc_f32",
                      cudaLaunchKernel(bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), dim3(Q.threads), b2, Q.smem_r, st));
         }
         void *a3[] = {(void *)&dd, &pc, &T_r, &pc1, &T_r1, &wsv};
@@ -1052,12 +1053,14 @@ static void launch_batch_plain_init(pcg_ctx *ctx, const BatchWs &ws, int grid) {
 static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int RP, int RG,
                                 BatchProducts *bp, bool with_tail) {
     *bp = BatchProducts{};
-    const bool df = ctx->opt.precision == PCG_PREC_DF32;
+    const bool df = prec_pairs(ctx->opt.precision);
+    const bool fx = ctx->opt.precision == PCG_PREC_FX64;
     if ((RG == 0 || !ctx->tiled_enabled) && !df) return PCG_OK;
     if (RG == 0) RG = 1;   // double-float products exist only in tiled form
     char tag[32];
-    snprintf(tag, sizeof tag, "batch%d%s", RG, df ? "d" : "");
-    pcg_status st = build_tiled_plan(ctx, tag, Xr, Xc, RG, df ? kVtDF : kVtF32, RP / RG, true, &bp->plan);
+    snprintf(tag, sizeof tag, "batch%d%s", RG, fx ? "x" : df ? "d" : "");
+    const int vt = tiled_vtype(ctx->opt.precision);
+    pcg_status st = build_tiled_plan(ctx, tag, Xr, Xc, RG, vt, RP / RG, true, &bp->plan);
     if (st != PCG_OK) return st;
     if (!bp->plan.valid) return PCG_OK;
     st = tiled_prepare(ctx, bp->plan, &bp->tk);
@@ -1068,14 +1071,15 @@ static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *
     if (!bp->pc_all) return cuda_error(ctx, e, "allocating the batched partials");
     bp->RG = RG;
     bp->df = df;
+    bp->fx = fx;
     // PCG_BETA_BATCH_TAIL=0 in the environment keeps the main plan to the end
     const char *tail_env = getenv("PCG_BETA_BATCH_TAIL");
     if (with_tail && RG >= 2 && !(tail_env && tail_env[0] == '0')) {
         // group width 1 for the last live chain: half the staged bytes per
         // gather of the main plan's width-RG groups
         char tag1[32];
-        snprintf(tag1, sizeof tag1, "batchtail%s", df ? "d" : "");
-        st = build_tiled_plan(ctx, tag1, Xr, Xc, 1, df ? kVtDF : kVtF32, 1, true, &bp->plan1);
+        snprintf(tag1, sizeof tag1, "batchtail%s", fx ? "x" : df ? "d" : "");
+        st = build_tiled_plan(ctx, tag1, Xr, Xc, 1, vt, 1, true, &bp->plan1);
         if (st != PCG_OK) return st;
         if (bp->plan1.valid) {
             st = tiled_prepare(ctx, bp->plan1, &bp->tk1);
@@ -1165,7 +1169,7 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
     if (force && force[0]) {
         const int v = atoi(force);
         *rg_out = (v == 1 || v == 2 || v == 4 || v == 8) && v <= RP ? v : 0;
-        if (ctx->opt.precision == PCG_PREC_DF32 && (*rg_out == 0 || *rg_out > 4)) *rg_out = 4 <= RP ? 4 : RP;
+        if (prec_pairs(ctx->opt.precision) && (*rg_out == 0 || *rg_out > 4)) *rg_out = 4 <= RP ? 4 : RP;
         return PCG_OK;
     }
     char key[128];
@@ -1202,7 +1206,7 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
         PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
         float best = 1e30f;
         const int cands[] = {0, 1, 2, 4, 8};
-        const bool df = ctx->opt.precision == PCG_PREC_DF32;
+        const bool df = prec_pairs(ctx->opt.precision);
         for (int rg : cands) {
             if (rg > RP || (df && (rg == 0 || rg > 4))) continue;
             BatchProducts bp;
@@ -1254,7 +1258,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
                        const double *tau, const double *eta, const double *delta, double tol,
                        int max_iter, double *beta, int *iters, double *resid, int *status) {
     if (ctx->opt.precision == PCG_PREC_FP64)
-        return set_error(ctx, PCG_BADARG, "the batched path computes its products in float32 arithmetic: use PCG_PREC_FP32_REFINED, PCG_PREC_FP32 or PCG_PREC_DF32");
+        return set_error(ctx, PCG_BADARG, "the batched path computes its products in float32 arithmetic: use PCG_PREC_FP32_REFINED, PCG_PREC_FP32, PCG_PREC_DF32 or PCG_PREC_FX64");
     int RP = 4;
     while (RP < nrhs) RP *= 2;
     const int64_t n = std::max<int64_t>(Xr->n, 1), p = std::max<int64_t>(Xr->p, 1);
@@ -1322,7 +1326,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     d.stop_rule = ctx->opt.stop_rule;
     d.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
-    d.df = ctx->opt.precision == PCG_PREC_DF32 ? 1 : 0;
+    d.df = prec_pairs(ctx->opt.precision) ? 1 : 0;
     const bool refined = d.refined != 0;
     int RG = 0;
     pcg_status st = choose_rg(ctx, Xr, Xc, ws, d, hd, RP, refined, nrhs, hsc, hflags, &RG);

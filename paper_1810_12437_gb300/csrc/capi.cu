@@ -224,7 +224,7 @@ pcg_status pcg_ctx_create(pcg_ctx **out, const pcg_options *opt, void *stream) {
     pcg_ctx *ctx = new pcg_ctx();
     if (opt) ctx->opt = *opt;
     else pcg_options_default(&ctx->opt);
-    if (ctx->opt.precision < 0 || ctx->opt.precision > 3 || ctx->opt.stop_rule < 0 ||
+    if (ctx->opt.precision < 0 || ctx->opt.precision > PCG_PREC_FX64 || ctx->opt.stop_rule < 0 ||
         ctx->opt.stop_rule > 1 || ctx->opt.reliable_k < 0) {
         delete ctx;
         return PCG_BADARG;

@@ -16,6 +16,10 @@ namespace pcg {
 constexpr int kMaxBatch = 32;          // largest RHS block of the batched path
 constexpr int kMaxReduceBlocks = 4096; // capacity of the grid-reduction partial buffers
 
+// Precisions whose vectors (s, omega) and product partials are float pairs:
+// double-float sums, or fixed-point sums of each tile (PCG_PREC_FX64).
+inline bool prec_pairs(int precision) { return precision == PCG_PREC_DF32 || precision == PCG_PREC_FX64; }
+
 // Per-chain CG state kept in device memory.  Written only by the single
 // "last block" of a grid reduction, read by every later kernel.
 struct CgScalars {

@@ -586,7 +586,7 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
     A.om32 = ctx->ws.om32;
     A.want_w = d.rhs == nullptr ? 1 : 0;
     A.want_om32 = f32 ? 1 : 0;
-    const bool df = precision == PCG_PREC_DF32;
+    const bool df = prec_pairs(precision);
     A.s_gather = f32 ? (const void *)ctx->ws.s32 : (const void *)ctx->ws.s64;
     A.om = f32 ? (const void *)ctx->ws.om32 : nullptr;   // NULL: float64 omega from the descriptor
     A.u = ctx->ws.u;
@@ -704,8 +704,14 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
 // Plain launches (use_graph = 0): same kernels, host check every 8 iterations.
 static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, const TiledPlan &tp) {
     const SingleLaunch L = single_launch(ctx, d);
-    const char *csr_name = precision == PCG_PREC_DF32 ? "t_csr_df32" : precision == PCG_PREC_FP64 ? "t_csr_f64" : "t_csr_f32";
-    const char *csc_name = precision == PCG_PREC_DF32 ? "t_csc_df32" : precision == PCG_PREC_FP64 ? "t_csc_f64" : "t_csc_f32";
+    const char *csr_name = precision == PCG_PREC_DF32   ? "t_csr_df32"
+                           : precision == PCG_PREC_FX64 ? "t_csr_fx64"
+                           : precision == PCG_PREC_FP64 ? "t_csr_f64"
+                                                        : "t_csr_f32";
+    const char *csc_name = precision == PCG_PREC_DF32   ? "t_csc_df32"
+                           : precision == PCG_PREC_FX64 ? "t_csc_fx64"
+                           : precision == PCG_PREC_FP64 ? "t_csc_f64"
+                                                        : "t_csc_f32";
     TiledKernels TK{};
     if (tp.valid) {
         pcg_status st = tiled_prepare(ctx, tp, &TK);
@@ -717,7 +723,7 @@ static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, cons
     const DrawDesc *dd = ws.desc;
     cudaStream_t st = ctx->stream;
     const int B = L.threads;
-    const bool df = precision == PCG_PREC_DF32;
+    const bool df = prec_pairs(precision);
     PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32,
                                                                 (tp.valid && !f32 && !df) ? ws.om64 : nullptr,
                                                                 (tp.valid && df) ? ws.omdf : nullptr));
@@ -777,7 +783,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     DrawDesc d = din;
     d.refined = (precision == PCG_PREC_FP32_REFINED) ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
-    d.df = precision == PCG_PREC_DF32 ? 1 : 0;
+    d.df = prec_pairs(precision) ? 1 : 0;
     *ctx->h_desc = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
                                       cudaMemcpyHostToDevice, ctx->stream));
@@ -785,7 +791,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     if (ctx->tiled_enabled) {
         const pcg_csr xr{d.n, d.p, d.nnz, d.row_ptr, d.col_idx};
         const pcg_csc xc{d.n, d.p, d.nnz, d.col_ptr, d.row_idx};
-        const int vt = precision == PCG_PREC_FP64 ? kVtF64 : precision == PCG_PREC_DF32 ? kVtDF : kVtF32;
+        const int vt = tiled_vtype(precision);
         st = build_tiled_plan(ctx, "single", &xr, &xc, 1, vt, 1, true, &tp);
         if (st != PCG_OK) return st;
     }
@@ -894,7 +900,7 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
     const bool f32 = prec == PCG_PREC_FP32 || prec == PCG_PREC_FP32_REFINED;
     TiledPlan tp{};
     if (ctx->tiled_enabled) {
-        const int vt = prec == PCG_PREC_FP64 ? kVtF64 : prec == PCG_PREC_DF32 ? kVtDF : kVtF32;
+        const int vt = tiled_vtype(prec);
         pcg_status st2 = build_tiled_plan(ctx, "single", Xr, Xc, 1, vt, 1, false, &tp);
         if (st2 != PCG_OK) return st2;
     }
@@ -903,7 +909,7 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
         pcg_status st2 = tiled_prepare(ctx, tp, &TK);
         if (st2 != PCG_OK) return st2;
         TiledArgs ta{tp};
-        const bool df = prec == PCG_PREC_DF32;
+        const bool df = prec_pairs(prec);
         if (f32) PCG_PROF(ctx, "to_f32", k_to_f32<<<grid, 256, 0, s>>>(v, ws.s32, d.p));
         if (df) PCG_PROF(ctx, "to_df", k_to_df<<<grid, 256, 0, s>>>(v, ws.sdf, d.p));
         PCG_PROF(ctx, "rhs_w", k_rhs_w<<<grid, 256, 0, s>>>(ws.desc, nullptr, ws.om32, 0, f32 ? 1 : 0,

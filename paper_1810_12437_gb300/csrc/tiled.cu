@@ -123,6 +123,16 @@ __global__ void k_plan_sentinel(uint16_t *__restrict__ chunk, int W) {
     if (threadIdx.x < 8) chunk[threadIdx.x] = (uint16_t)W;
 }
 
+// *out = max(*out, most chunks of one segment in one tile) (bounds the number
+// of values a fixed-point segment sum adds; *out starts at 0)
+__global__ void k_plan_maxch(const uint32_t *__restrict__ chunks, int64_t nts, int *__restrict__ out) {
+    uint32_t m = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nts; q += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, chunks[q]);
+    m = __reduce_max_sync(kFull, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (int)min(m, (uint32_t)INT32_MAX));
+}
+
 // Work split: split[t * (nwt + 1) + k] = first segment of the k-th of nwt
 // warps in tile t, chosen so that the warps get equal costs, a segment's cost
 // being its chunks plus kSegCost (its bounds, reduction and output)
@@ -429,7 +439,7 @@ __global__ void __launch_bounds__(kPermWarps * 32)
 static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr,
                             const int32_t *idx, int64_t nseg, int64_t nnz, int W, int T, int nwt,
                             int value_bytes, bool bank_order, uint16_t **out_idx, uint32_t **out_cb,
-                            int32_t **out_split, uint32_t *out_sent, int32_t **out_keys) {
+                            int32_t **out_split, uint32_t *out_sent, int32_t **out_keys, int *out_maxch) {
     cudaError_t e;
     const int64_t nb = (int64_t)(T + 1) * nseg;
     const int64_t nts = (int64_t)T * nseg;
@@ -470,6 +480,7 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
                                                       0, 32 + tbits, s));
     PCG_PROF(ctx, "plan_chunks", k_plan_chunks_sorted<<<grid, 256, 0, s>>>(bounds, order, nseg, T, chunks));
     PCG_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, scan_bytes, chunks, cb, (int)nc, s));
+    k_plan_maxch<<<grid, 256, 0, s>>>(chunks, nts, out_maxch);
     PCG_PROF(ctx, "plan_fill", k_plan_fill_sorted<<<grid, 256, 0, s>>>(idx, bounds, order, cb, nseg, T, W, pidx));
     const uint32_t sent = (uint32_t)(cap / 8 - 1);
     k_plan_sentinel<<<1, 32, 0, s>>>(pidx + (size_t)sent * 8, W);
@@ -494,7 +505,7 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
                             int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl) {
     *pl = TiledPlan{};
-    const int vsize = vtype == kVtF32 ? 4 : 8;   // staged bytes per value (DF: two floats)
+    const int vsize = vtype == kVtF32 ? 4 : 8;   // staged bytes per value (DF: two floats; FX: int64)
     pl->vtype = vtype;
     const int64_t n = Xr->n, p = Xr->p, nnz = Xr->nnz;
     // positions are 32-bit inside the kernels (padding included)
@@ -530,12 +541,16 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     // that serve a whole solve
     const bool bank_order = ctx->bank_permute && many_products;
     cudaError_t e;
+    pl->maxch = (int *)grow(ctx, t + ":maxch", 2 * sizeof(int), &e);
+    if (!pl->maxch) return cuda_error(ctx, e, "allocating the tiled plan");
+    PCG_CUDA_TRY(ctx, cudaMemsetAsync(pl->maxch, 0, 2 * sizeof(int), ctx->stream));
     pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, n, nnz, pl->W_c, pl->T_c,
                               pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt,
-                              &pl->split_r, &pl->sent_r, &pl->row_keys);
+                              &pl->split_r, &pl->sent_r, &pl->row_keys, pl->maxch);
     if (st != PCG_OK) return st;
     st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, p, nnz, pl->W_r, pl->T_r, pl->csc_chunks * pl->nw,
-                   RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c, &pl->sent_c, &pl->col_keys);
+                   RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c, &pl->sent_c, &pl->col_keys,
+                   pl->maxch + 1);
     if (st != PCG_OK) return st;
     // partial sums: float for float values, double otherwise (DF included);
     // row partials per group, column partials of one group (callers with
@@ -579,15 +594,117 @@ struct Tr<DF> {
     using part = float2;
     using src = float2;
 };
+template <>
+struct Tr<FX> {
+    using smem = long long;   // the value times 2^k, rounded (k: the tile's scale exponent)
+    using part = float2;
+    using src = float2;
+};
 
 template <typename T>
 __device__ __forceinline__ typename Tr<T>::smem smem_zero() { return typename Tr<T>::smem(0); }
 template <>
 __device__ __forceinline__ float2 smem_zero<DF>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ long long smem_zero<FX>() { return 0ll; }
 template <typename T>
 __device__ __forceinline__ typename Tr<T>::src src_zero() { return typename Tr<T>::src(0); }
 template <>
 __device__ __forceinline__ float2 src_zero<DF>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ float2 src_zero<FX>() { return make_float2(0.f, 0.f); }
+
+// ---------------------------------------------------------------------------
+// Fixed point (FX).  A CTA stages its tile of float pairs (hi + lo), takes the
+// largest |hi| of each right-hand side r over the tile, and picks k_r so that
+// every value of r times 2^k_r stays below 2^(61 - hb), where a segment of the
+// pass adds fewer than 2^hb values (hb: bits of 8 x the plan's most chunks in
+// one segment and tile).  Each value becomes round(hi 2^k) + round(lo 2^k) as
+// a 64-bit integer, so every segment sum is exact and below 2^61; the grid
+// step 2^-k_r is 2^(hb - 60) of r's largest value in the tile or less.  A sum
+// is returned as a float pair times 2^-k_r.  The conversions use integer and
+// float32 instructions only (GB300 runs 64-bit float/integer conversions at
+// the float64 rate).
+// ---------------------------------------------------------------------------
+constexpr int kFxNonFinite = INT32_MIN;   // scale of a tile holding NaN or Inf
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }   // -126 <= e <= 127
+
+// k for a tile whose largest |hi| has float bits mb
+__device__ __forceinline__ int fx_scale(uint32_t mb, int maxch) {
+    if (mb >= 0x7f800000u) return kFxNonFinite;
+    if (mb == 0u) return 0;
+    const int e = max(1, (int)(mb >> 23));                   // |value| < 2^(e - 126)
+    const int hb = 32 - __clz(8 * max(1, maxch));            // a segment adds fewer than 2^hb values
+    return 187 - hb - e;                                     // 61 - hb - (e - 126)
+}
+
+// round(x 2^k) for |x 2^k| < 2^58, from the bits of x: x = m 2^E with an
+// integer mantissa m < 2^24, so x 2^k = m 2^s, shifted left, or right with
+// rounding to nearest (halves away from zero)
+__device__ __forceinline__ long long fx_round(float x, int k) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    const uint32_t m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int s = (e ? e : 1) - 150 + k;
+    long long q;
+    if (s >= 0) q = (long long)((unsigned long long)m << s);
+    else if (s >= -24) q = (long long)((m + (1u << (-s - 1))) >> (-s));
+    else q = 0;
+    return (b >> 31) ? -q : q;
+}
+
+__device__ __forceinline__ long long fx_from_pair(float2 v, int k) {
+    if (k == kFxNonFinite) return 0ll;
+    return fx_round(v.x, k) + fx_round(v.y, k);
+}
+
+// q 2^-k as a float pair: q = p2 2^42 + p1 2^21 + p0 with pieces of at most 21
+// bits (each an exact float), summed with TwoSum; |k| <= 187 applied as two
+// exact power-of-two products
+__device__ __forceinline__ float2 fx_to_pair(long long q, int k) {
+    if (k == kFxNonFinite) return make_float2(__int_as_float(0x7fc00000), 0.f);
+    const int p2 = (int)(q >> 42);                                     // |p2| < 2^20 (|q| < 2^62)
+    const uint32_t r = (uint32_t)((((unsigned long long)q) >> 21) & 0x1fffffull);        // bits 21..41
+    const uint32_t p0 = (uint32_t)q & 0x1fffffu;
+    const float a = __int2float_rn(p2) * 4398046511104.f;             // 2^42
+    const float b = __uint2float_rn(r) * 2097152.f;                    // 2^21
+    float t, e, t2, e2;
+    two_sum(a, b, t, e);
+    two_sum(t, __uint2float_rn(p0), t2, e2);
+    const float2 d = df_norm(t2, __fadd_rn(e, e2));
+    const float t1 = pow2f(-(k >> 1)), t3 = pow2f(-(k - (k >> 1)));
+    return make_float2(d.x * t1 * t3, d.y * t1 * t3);
+}
+
+// Per right-hand side scales of a CTA: thread values m0 (for r0) and m1 (for
+// r0 + 1, when two == true) are the largest |hi| bits it staged; every thread
+// of a warp with the same lane % span holds the same r0.  Writes k_r to
+// sk[0..RG) (red: 32 * 8 words of shared memory); ends with a barrier.
+template <int RG>
+__device__ __forceinline__ void fx_scales(uint32_t m0, uint32_t m1, bool two, int span, int maxch,
+                                          uint32_t *red, int *sk) {
+    for (int o = 16; o >= span; o >>= 1) {
+        m0 = max(m0, __shfl_xor_sync(kFull, m0, o));
+        m1 = max(m1, __shfl_xor_sync(kFull, m1, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane < span) {
+        if (two) {
+            red[w * RG + 2 * lane] = m0;
+            red[w * RG + 2 * lane + 1] = m1;
+        } else {
+            red[w * RG + lane] = m0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < RG) {
+        uint32_t M = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) M = max(M, red[q * RG + threadIdx.x]);
+        sk[threadIdx.x] = fx_scale(M, maxch);
+    }
+    __syncthreads();
+}
 
 // u = omega * (sum of row partials), in the staged type
 __device__ __forceinline__ float scale_part(float o, float a) { return o * a; }
@@ -606,6 +723,7 @@ struct Vec {
 #pragma unroll
             for (int r = 0; r < RG; ++r) v[k][r] = T(0);
     }
+    __device__ __forceinline__ void bind(const int *) {}
     template <int K>
     __device__ __forceinline__ void add_smem(const T *base) {   // base: shared memory
         if constexpr (sizeof(T) == 4 && RG % 4 == 0) {
@@ -656,6 +774,7 @@ template <int RG>
 struct Vec<DF, RG> {
     static constexpr int NP = RG >= 2 ? RG / 2 : 1;   // packed pairs (RG = 1: scalar)
     float2 s[2][NP], c[2][NP];
+    __device__ __forceinline__ void bind(const int *) {}
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -722,16 +841,68 @@ struct Vec<DF, RG> {
     }
 };
 
-// Writes value r of a staged row (the split layout above for double-float).
-template <typename T, int RG>
-__device__ __forceinline__ void store_staged(typename Tr<T>::smem *row, int r, typename Tr<T>::smem v) {
+// Fixed-point sums (see FX above): exact integer additions in two sets.
+template <int RG>
+struct Vec<FX, RG> {
+    long long a[2][RG];
+    int k[RG];   // the tile's scale exponent of each right-hand side
+    __device__ __forceinline__ void bind(const int *sk) {
+#pragma unroll
+        for (int r = 0; r < RG; ++r) k[r] = sk[r];
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) a[j][r] = 0ll;
+    }
+    template <int K>
+    __device__ __forceinline__ void add_smem(const long long *base) {
+        if constexpr (RG == 1) {
+            a[K][0] += base[0];
+        } else {
+#pragma unroll
+            for (int r = 0; r < RG; r += 2) {
+                const longlong2 x = *reinterpret_cast<const longlong2 *>(base + r);
+                a[K][r] += x.x;
+                a[K][r + 1] += x.y;
+            }
+        }
+    }
+    __device__ __forceinline__ void reduce(int lg) {
+#pragma unroll
+        for (int r = 0; r < RG; ++r) a[0][r] += a[1][r];
+        for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
+#pragma unroll
+            for (int r = 0; r < RG; ++r) a[0][r] += __shfl_xor_sync(kFull, a[0][r], o);
+        }
+    }
+    __device__ __forceinline__ float2 out(int r) const { return fx_to_pair(a[0][r], k[r]); }
+};
+
+// Writes value r of a staged row (the split layout above for double-float;
+// fixed point stages each value as its float pair, converted in place later).
+template <typename T, int RG, typename V>
+__device__ __forceinline__ void store_staged(typename Tr<T>::smem *row, int r, V v) {
     if constexpr (std::is_same<T, DF>::value) {
         float *f = reinterpret_cast<float *>(row);
         f[r] = v.x;
         f[RG + r] = v.y;
+    } else if constexpr (std::is_same<T, FX>::value) {
+        reinterpret_cast<float2 *>(row)[r] = v;
     } else {
         row[r] = v;
     }
+}
+
+// Fixed point: converts the CTA's staged float pairs [0, nvals) (value t
+// belongs to right-hand side t % RG) to int64 in place with the scales sk.
+// blockDim.x is a multiple of RG, so a thread's values share one r.
+template <int RG>
+__device__ __forceinline__ void fx_convert(long long *sv, int64_t nvals, const int *sk) {
+    const int k = sk[threadIdx.x % RG];
+    float2 *f = reinterpret_cast<float2 *>(sv);
+    for (int64_t t = threadIdx.x; t < nvals; t += blockDim.x) sv[t] = fx_from_pair(f[t], k);
 }
 
 // Adds the gathered values of one whole chunk of 8 indices (pad slots point
@@ -761,6 +932,7 @@ __device__ __forceinline__ void chunk_add(const uint4 w, const typename Tr<T>::s
 // round, or the first of the next round) is loaded before the current one is
 // summed, so 2 kBlk chunks per lane are in flight.  Segment s's chunks are
 // [cb[s], cb[s + 1]); its sum goes to out[(keys ? keys[s] : s) * ostride + r].
+// fxk: the tile's fixed-point scale exponent of each right-hand side (FX only).
 struct SegRound {
     uint32_t q0, q1;   // this lane's segment's chunks
     int64_t key;
@@ -800,7 +972,8 @@ template <typename T, int RG>
 __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, const uint32_t *__restrict__ cb,
                                               int sA, int sB, const typename Tr<T>::smem *__restrict__ sv,
                                               uint32_t sent, const int32_t *__restrict__ keys,
-                                              typename Tr<T>::part *__restrict__ out, int64_t ostride) {
+                                              typename Tr<T>::part *__restrict__ out, int64_t ostride,
+                                              const int *fxk) {
     if (sA >= sB) return;
     const int lane = threadIdx.x & 31;
     const int lg = lanes_log2(__ldg(cb + sB) - __ldg(cb + sA), (uint32_t)(sB - sA));
@@ -813,6 +986,7 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
     uint4 A[kBlk];
     load_block(A, w4, cur, 0, ln, lg, sent);
     Vec<T, RG> acc;
+    acc.bind(fxk);
     acc.zero();
     for (;;) {
         // the block after this one: in this round, or the first of the next
@@ -868,6 +1042,8 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int64_t j0 = (int64_t)c * P.W_c;
     const int64_t total = min((int64_t)P.W_c, P.p - j0) * RG;
     const int off = s_off + g * RG;
+    constexpr bool fx = std::is_same<T, FX>::value;
+    uint32_t mb = 0;   // fixed point: largest |hi| this thread staged (float bits)
     // stage the tile's slice of s, kStageUnroll loads in flight per thread
     for (int64_t t0 = threadIdx.x; t0 < total; t0 += (int64_t)kStageUnroll * blockDim.x) {
         SRC v[kStageUnroll];
@@ -880,16 +1056,23 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
         for (int k = 0; k < kStageUnroll; ++k) {
             const int64_t t = t0 + (int64_t)k * blockDim.x;
             if (t < total) store_staged<T, RG>(sS + (t / RG) * RG, (int)(t % RG), v[k]);
+            if constexpr (fx) mb = max(mb, __float_as_uint(fabsf(v[k].x)));   // zero past the end
         }
     }
     if (threadIdx.x < RG) sS[(size_t)P.W_c * RG + threadIdx.x] = smem_zero<T>();   // pad sentinel
+    __shared__ int fxk[8];
+    if constexpr (fx) {
+        __shared__ uint32_t red[32 * 8];
+        fx_scales<RG>(mb, 0u, false, RG, __ldg(P.maxch), red, fxk);   // thread's values: r = tid % RG
+        fx_convert<RG>(sS, total, fxk);
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     const int32_t *__restrict__ sp = P.split_r + (size_t)c * (P.csr_blocks * P.nw + 1) + b * P.nw + warp;
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + ((size_t)g * P.T_c + c) * (size_t)P.n * RG;
     warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.col16), P.rt + (size_t)c * P.n, sA, sB, sS,
-                         P.sent_r, P.row_keys + (size_t)c * P.n, Pr, RG);
+                         P.sent_r, P.row_keys + (size_t)c * P.n, Pr, RG, fxk);
 }
 
 // ---------------------------------------------------------------------------
@@ -946,6 +1129,9 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(
         reinterpret_cast<const SM *>(P.U) + (size_t)g * P.u_stride + (size_t)r0 * RG);
     uint4 *dst = reinterpret_cast<uint4 *>(smem_raw);
+    constexpr bool fx = std::is_same<T, FX>::value;
+    const int64_t nvals = min((int64_t)P.W_r, n - r0) * RG;
+    uint32_t mb = 0, mb1 = 0;   // fixed point: largest |hi| of the even and odd values this thread copied
     for (int64_t w0 = threadIdx.x; w0 < words; w0 += (int64_t)kStageUnroll * blockDim.x) {
         uint4 v[kStageUnroll];
 #pragma unroll
@@ -956,10 +1142,26 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
 #pragma unroll
         for (int k = 0; k < kStageUnroll; ++k) {
             const int64_t w = w0 + (int64_t)k * blockDim.x;
-            if (w < words) dst[w] = v[k];
+            if (w < words) {
+                dst[w] = v[k];
+                if constexpr (fx) {   // |hi| of values 2w and 2w + 1 (the last word may run past the strip)
+                    mb = max(mb, v[k].x & 0x7fffffffu);
+                    if (2 * w + 1 < nvals) mb1 = max(mb1, v[k].z & 0x7fffffffu);
+                }
+            }
         }
     }
-    __syncthreads();   // the pad sentinel may share the last copied word
+    __shared__ int fxk[8];
+    if constexpr (fx) {
+        // a thread's words hold values 2w, 2w + 1 with w = tid (mod 2), so
+        // r0 = 2 tid % RG, and r0 + 1 for RG >= 2; fx_scales ends with a barrier
+        __shared__ uint32_t red[32 * 8];
+        if constexpr (RG == 1) fx_scales<RG>(max(mb, mb1), 0u, false, 1, __ldg(P.maxch + 1), red, fxk);
+        else fx_scales<RG>(mb, mb1, true, RG / 2, __ldg(P.maxch + 1), red, fxk);
+        fx_convert<RG>(sU, nvals, fxk);
+    } else {
+        __syncthreads();   // the pad sentinel may share the last copied word
+    }
     if (threadIdx.x < RG) sU[(size_t)P.W_r * RG + threadIdx.x] = smem_zero<T>();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
@@ -967,7 +1169,7 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pc = pc_out + (size_t)t * p * pc_stride + pc_off + g * RG;
     warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.row16), P.cs + (size_t)t * p, sA, sB, sU,
-                         P.sent_c, P.col_keys + (size_t)t * p, Pc, pc_stride);
+                         P.sent_c, P.col_keys + (size_t)t * p, Pc, pc_stride, fxk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1049,7 +1251,7 @@ uint64_t plan_fingerprint(const TiledPlan &pl) {
         }
     };
     const void *ptrs[] = {pl.col16, pl.row16, pl.rt, pl.cs, pl.row_keys, pl.col_keys, pl.split_r, pl.split_c,
-                          pl.Pr, pl.Pc, pl.U};
+                          pl.Pr, pl.Pc, pl.U, pl.maxch};
     for (const void *q : ptrs) mix((uint64_t)(uintptr_t)q);
     const int64_t vals[] = {pl.valid, pl.RG, pl.vsize, pl.vtype, pl.ngroups, pl.n, pl.p, pl.nnz, pl.W_c, pl.T_c,
                             pl.W_r, pl.T_r, pl.u_stride, pl.csr_blocks, pl.csc_chunks, pl.threads, pl.nw,
@@ -1069,6 +1271,11 @@ TiledKernels tiled_kernels(const TiledPlan &pl) {
         k.csr = csr_ptr_rg<DF>(pl.RG);
         k.u = u_ptr_rg<DF>(pl.RG);
         k.csc = csc_ptr_rg<DF>(pl.RG);
+        k.fin1 = (void *)k_t_fin1<float2>;
+    } else if (pl.vtype == kVtFX) {
+        k.csr = csr_ptr_rg<FX>(pl.RG);
+        k.u = u_ptr_rg<FX>(pl.RG);
+        k.csc = csc_ptr_rg<FX>(pl.RG);
         k.fin1 = (void *)k_t_fin1<float2>;
     } else {
         k.csr = csr_ptr_rg<double>(pl.RG);

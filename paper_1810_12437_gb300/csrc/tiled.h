@@ -14,7 +14,17 @@ constexpr int kTileSmemBytes = 220 * 1024;   // staged slice of the gathered vec
 constexpr int kVtF32 = 0;   // float values, float sums
 constexpr int kVtF64 = 1;   // double values, double sums
 constexpr int kVtDF = 2;    // double-float pairs summed with TwoSum (float arithmetic)
+constexpr int kVtFX = 3;    // float pairs staged as 64-bit fixed point per tile, integer sums
 struct DF {};
+struct FX {};
+
+// value type of the tiled products for a precision (PCG_PREC_*)
+inline int tiled_vtype(int precision) {
+    return precision == PCG_PREC_FP64 ? kVtF64
+         : precision == PCG_PREC_DF32 ? kVtDF
+         : precision == PCG_PREC_FX64 ? kVtFX
+                                      : kVtF32;
+}
 constexpr size_t kSmemPerSm = 228 * 1024;     // shared memory of one SM
 // threads of a tiled-product CTA (one CTA per SM): 24 warps, or 16 when a
 // gathered value is wider than 16 bytes (more registers per thread)
@@ -46,6 +56,7 @@ struct TiledPlan {
     int64_t u_stride;         // values per group in U (n * RG, padded to 256 bytes)
     int csr_blocks, csc_chunks, threads, nw;
     uint32_t sent_r, sent_c;  // the sentinel chunk (8 zero-slot entries) of each index array
+    int *maxch;               // device, [2]: most chunks of one segment in one tile (CSR, CSC pass)
     size_t smem_c, smem_r;    // dynamic shared memory of the two passes
 };
 
@@ -58,11 +69,13 @@ struct TiledKernels {
 };
 
 // grid of the u kernel (k_t_u, a grid-stride loop): blocks of 256 threads per
-// RHS group, two per SM at most (a launch whose groups are all gated off then
-// schedules few blocks)
+// RHS group, at most 8 per SM over all groups and at least 2 per SM and group
+// (a launch whose groups are all gated off then schedules few blocks)
 inline int tiled_u_blocks(const TiledPlan &pl, int num_sms) {
     const int64_t need = (pl.n * pl.RG + 255) / 256;
-    return (int)(need < (int64_t)num_sms * 2 ? (need > 0 ? need : 1) : (int64_t)num_sms * 2);
+    const int per_sm = pl.ngroups >= 4 ? 2 : 8 / (pl.ngroups > 0 ? pl.ngroups : 1);
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
 // Builds (on the context stream) the 16-bit index copies, tile bounds and

@@ -561,7 +561,7 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
     G.stop_rule = ctx->opt.stop_rule;
     // the persistent kernel has float32 and float64 products: the double-float
     // mode runs as float32 with float64 recomputation of r
-    G.refined = (ctx->opt.precision == PCG_PREC_FP32_REFINED || ctx->opt.precision == PCG_PREC_DF32) ? 1 : 0;
+    G.refined = (ctx->opt.precision == PCG_PREC_FP32_REFINED || prec_pairs(ctx->opt.precision)) ? 1 : 0;
     G.reliable_k = ctx->opt.reliable_k;
     G.idle_limit_ns = 2000000000ll;   // 2 s without any completed tile anywhere
     *hg = G;

@@ -77,3 +77,13 @@ def test_build_script_targets_sm103a():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     for src in build.SOURCES:
         assert os.path.exists(os.path.join(build.CSRC, src))
+
+
+def test_precision_names_match_header():
+    """The binding's precision names carry the header's PCG_PREC_* values."""
+    import os
+    import re
+    from paper_1810_12437_gb300._native import PREC
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pcg_beta.h")).read()
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"PCG_PREC_(\w+)\s*=\s*(\d+)", hdr)}
+    assert enum == PREC

@@ -104,12 +104,13 @@ def test_batched_graph_and_plain_agree(pb, small3):
     assert np.array_equal(outs[0][1], outs[1][1])
 
 
-def test_batched_df32_matches_oracle(pb, small3):
-    """Double-float products in the batched path: per chain, iteration counts
-    in the float64 band of the oracle's and draws within 1e-6."""
+@pytest.mark.parametrize("prec", ["df32", "fx64"])
+def test_batched_pair_products_match_oracle(pb, small3, prec):
+    """Double-float and fixed-point products in the batched path: per chain,
+    iteration counts in the float64 band of the oracle's and draws within 1e-5."""
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
-    ctx = pb.Context(precision="df32")
+    ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
     beta = res.beta.cpu().numpy()
     for r in range(16):
@@ -119,15 +120,16 @@ def test_batched_df32_matches_oracle(pb, small3):
         assert rel(beta[r], ref) < 1e-5, r
 
 
+@pytest.mark.parametrize("prec", ["df32", "fx64"])
 @pytest.mark.parametrize("rg", ["1", "2", "4"])
-def test_batched_df32_every_group_width(pb, small3, rg, monkeypatch):
-    """Double-float products in groups of 1, 2 and 4 right-hand sides (one
-    launch covers every group): per chain, float64-band iteration counts and
-    draws within 1e-5 of the oracle."""
+def test_batched_pair_products_every_group_width(pb, small3, rg, prec, monkeypatch):
+    """Double-float and fixed-point products in groups of 1, 2 and 4
+    right-hand sides (one launch covers every group): per chain, float64-band
+    iteration counts and draws within 1e-5 of the oracle."""
     monkeypatch.setenv("PCG_BETA_BATCH_RG", rg)
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
-    ctx = pb.Context(precision="df32")
+    ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
     beta = res.beta.cpu().numpy()
     for r in (0, 3, 8, 15):
@@ -137,7 +139,8 @@ def test_batched_df32_every_group_width(pb, small3, rg, monkeypatch):
         assert rel(beta[r], ref) < 1e-5, r
 
 
-def test_batched_tail_plan(pb, small3, monkeypatch):
+@pytest.mark.parametrize("prec", ["df32", "fx64"])
+def test_batched_tail_plan(pb, small3, prec, monkeypatch):
     """With group width 2, a group-width-1 plan takes over the products when
     one chain is left (it gathers half the bytes per nonzero): draws with and
     without it both match the oracle, and the tail plan's launches appear in
@@ -148,7 +151,7 @@ def test_batched_tail_plan(pb, small3, monkeypatch):
     runs = {}
     for flag in ("1", "0"):
         monkeypatch.setenv("PCG_BETA_BATCH_TAIL", flag)
-        ctx = pb.Context(precision="df32")
+        ctx = pb.Context(precision=prec)
         res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
         runs[flag] = (res, pb.pcg_last_kernel_launches(ctx))
     assert runs["1"][1] > runs["0"][1]
@@ -189,14 +192,15 @@ def test_batched_full_size_true_residual(pb):
 
 
 @pytest.mark.slow
-def test_batched_full_size_df32_matches_oracle_samples(pb):
-    """The benchmark's launch (n = 5e5, p = 5e4, 16 chains, double-float
-    products): per chain the status and beta at the oracle's 64 sampled
-    coordinates (tests/golden/config3_oracle.json, written by a script that
-    runs only the oracle) within relative L2 1e-5, the true residual of three
-    chains within the stop rule, and the iteration count within 12 % of the
-    oracle's: on these chains (up to 3,369 iterations) the double-float counts
-    run 3-11 % below the oracle's sequential float64 sums, never above."""
+@pytest.mark.parametrize("prec", ["df32", "fx64"])
+def test_batched_full_size_pair_products_match_oracle_samples(pb, prec):
+    """The benchmark's launch (n = 5e5, p = 5e4, 16 chains, double-float or
+    fixed-point products): per chain the status and beta at the oracle's 64
+    sampled coordinates (tests/golden/config3_oracle.json, written by a script
+    that runs only the oracle) within relative L2 1e-5, the true residual of
+    three chains within the stop rule, and the iteration count within 12 % of
+    the oracle's: on these chains (up to 3,369 iterations) the double-float
+    counts run 3-11 % below the oracle's sequential float64 sums, never above."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "config3_oracle.json")) as f:
@@ -205,7 +209,7 @@ def test_batched_full_size_df32_matches_oracle_samples(pb):
     if P.X.nnz != gold["nnz"]:
         pytest.skip("the generated design differs from the one the golden file was made from")
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
-    ctx = pb.Context(precision="df32")
+    ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=20_000)
     beta = res.beta.cpu().numpy()
     for g in gold["chains"]:

@@ -57,8 +57,8 @@ def test_build_rhs_matches_oracle(pb, which, cfg1, cfg2):
 
 
 # ------------------------------------------------------------------ a3 + a4: Phi v
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("df32", 1e-12), ("fp32_refined", 3e-6),
-                                      ("fp32", 3e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("df32", 1e-12), ("fx64", 1e-12),
+                                      ("fp32_refined", 3e-6), ("fp32", 3e-6)])
 def test_phi_mul_matches_oracle(pb, cfg2, prec, tol):
     P = cfg2
     X, a = device_problem(P)
@@ -90,7 +90,7 @@ def well_conditioned():
 
 
 # ------------------------------------------------------------------ a2, a5-a7: same-k CG
-@pytest.mark.parametrize("prec", ["fp64", "df32"])
+@pytest.mark.parametrize("prec", ["fp64", "df32", "fx64"])
 @pytest.mark.parametrize("k", [1, 2, 5, 13, 30])
 def test_fixed_iterations_fp64(pb, k, prec):
     P = well_conditioned()
@@ -157,9 +157,10 @@ def test_draw_config2(pb, cfg2, prec, bound):
         assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df32"])
+@pytest.mark.parametrize("prec", ["fp64", "df32", "fx64"])
 def test_draw_config2_fp64(pb, cfg2, prec):
-    """float64 and double-float products: iteration counts in the float64 band."""
+    """float64, double-float and fixed-point products: iteration counts in the
+    float64 band."""
     P = cfg2
     X, a = device_problem(P)
     ctx = pb.Context(precision=prec)
@@ -290,10 +291,11 @@ def test_repeat_calls_deterministic(pb, cfg2):
 def test_bank_order_changes_only_rounding(pb, monkeypatch):
     """The plan's bank-aware entry order permutes entries inside segments:
     at a fixed iteration count on a well-conditioned instance, draws with and
-    without it agree to rounding (double-float and float32 products)."""
+    without it agree to rounding (double-float and float32 products), and
+    exactly with fixed-point products (integer sums do not depend on order)."""
     P = well_conditioned()
     X, a = device_problem(P)
-    for prec, tol in (("df32", 1e-11), ("fp32", 1e-5)):
+    for prec, tol in (("df32", 1e-11), ("fp32", 1e-5), ("fx64", 0.0)):
         outs = []
         for flag in ("1", "0"):
             monkeypatch.setenv("PCG_BETA_BANK_PERMUTE", flag)
@@ -301,4 +303,7 @@ def test_bank_order_changes_only_rounding(pb, monkeypatch):
             r = pb.pcg_draw_beta(ctx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"],
                                  tol=0.0, max_iter=20)
             outs.append(r.beta.cpu().numpy())
-        assert rel(outs[0], outs[1]) < tol, prec
+        if tol == 0.0:
+            assert np.array_equal(outs[0], outs[1]), prec
+        else:
+            assert rel(outs[0], outs[1]) < tol, prec

@@ -36,9 +36,10 @@ def small_batch(seed=0):
     return probs + [e, one]
 
 
-# df32 runs as fp32_refined in the persistent kernel (float32 products,
+# df32 and fx64 run as fp32_refined in the persistent kernel (float32 products,
 # float64 recomputation of r)
-@pytest.mark.parametrize("prec,bound", [("fp64", 1e-6), ("fp32_refined", 1e-5), ("df32", 1e-5), ("fp32", 1e-3)])
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-6), ("fp32_refined", 1e-5), ("df32", 1e-5), ("fx64", 1e-5),
+                                        ("fp32", 1e-3)])
 def test_uneven_matches_oracle(pb, prec, bound):
     probs = small_batch()
     ctx = pb.Context(precision=prec)
