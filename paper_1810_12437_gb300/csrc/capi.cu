@@ -234,6 +234,8 @@ pcg_status pcg_ctx_create(pcg_ctx **out, const pcg_options *opt, void *stream) {
     ctx->tiled_enabled = !(tiled && tiled[0] == '0');
     const char *perm = getenv("PCG_BETA_BANK_PERMUTE");
     ctx->bank_permute = !(perm && perm[0] == '0');
+    const char *pcache = getenv("PCG_BETA_PLAN_CACHE");
+    ctx->plan_cache_enabled = !(pcache && pcache[0] == '0');
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);

@@ -129,6 +129,10 @@ struct pcg_ctx {
     bool tiled_enabled = true;
     // bank-aware entry order in the tiled plan (on unless PCG_BETA_BANK_PERMUTE=0)
     bool bank_permute = true;
+    // tiled plans kept across calls (tiled.cu), per plan tag: the plan and the
+    // key and design-content hash it was built for (PCG_BETA_PLAN_CACHE=0: off)
+    std::map<std::string, std::vector<unsigned char>> plan_cache;
+    bool plan_cache_enabled = true;
 };
 
 namespace pcg {

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -167,14 +168,20 @@ __global__ void k_plan_split(const uint32_t *__restrict__ cb, int64_t nseg, int 
 }
 
 // lanes per segment (log2) for a warp whose segments hold `chunks` chunks in
-// all: one lane when they average at most two chunks (adjacent lanes then read
-// adjacent segments), else the fewest lanes (at least two, so that a group
-// reads whole sectors) that cover a typical segment with one block each
+// all: one lane when they average at most kLaneChunks chunks (adjacent lanes
+// then read adjacent segments), else the fewest lanes (at least two, so that a
+// group reads whole sectors) that cover a typical segment with kRoundBlocks
+// blocks each.  Longer rounds spread a round's fixed work (bounds, lane
+// reduction, output) over more chunks; measured on GB300, two blocks per lane
+// beat one by 6-17 % per product, and one lane up to 4 chunks beat up to 2 by
+// 3 % on the column pass.
+constexpr uint32_t kRoundBlocks = 2;
+constexpr uint32_t kLaneChunks = 4;
 __device__ __forceinline__ int lanes_log2(uint32_t chunks, uint32_t nseg) {
-    if (chunks <= 2u * nseg) return 0;
+    if (chunks <= kLaneChunks * nseg) return 0;
     const uint32_t mean = (chunks + nseg - 1) / nseg;
     int lg = 1;
-    while (lg < 5 && ((uint32_t)kBlk << lg) < mean) ++lg;
+    while (lg < 5 && ((uint32_t)(kRoundBlocks * kBlk) << lg) < mean) ++lg;
     return lg;
 }
 
@@ -502,6 +509,50 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
     return PCG_OK;
 }
 
+// splitmix64's finalizer
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// *out += a position-dependent hash of every entry of the design's four index
+// arrays (a sum of mixed (array, position, value) words, so the order in which
+// threads add does not matter; *out starts at 0)
+__global__ void k_design_hash(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int64_t *__restrict__ cp, const int32_t *__restrict__ ri, int64_t n,
+                              int64_t p, int64_t nnz, unsigned long long *__restrict__ out) {
+    unsigned long long h = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = tid; i < nnz; i += stride) {
+        const unsigned long long q = (unsigned long long)i << 2;
+        h += mix64(((unsigned long long)(uint32_t)__ldg(ci + i) << 32) ^ (q | 0ull) ^ 0x9e3779b97f4a7c15ull);
+        h += mix64(((unsigned long long)(uint32_t)__ldg(ri + i) << 32) ^ (q | 1ull) ^ 0xc2b2ae3d27d4eb4full);
+    }
+    for (int64_t i = tid; i <= n; i += stride)
+        h += mix64(mix64((unsigned long long)__ldg(rp + i)) ^ (((unsigned long long)i << 2) | 2ull));
+    for (int64_t i = tid; i <= p; i += stride)
+        h += mix64(mix64((unsigned long long)__ldg(cp + i)) ^ (((unsigned long long)i << 2) | 3ull));
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, h);
+}
+
+// A cached plan: valid while the design's pointers, sizes and content (hash)
+// and the plan's parameters are those it was built for.
+struct PlanCacheEntry {
+    uint64_t key, content;
+    TiledPlan plan;
+};
+
+static uint64_t fnv_mix(uint64_t h, uint64_t v) {
+    for (int k = 0; k < 8; ++k) {
+        h ^= (v >> (8 * k)) & 0xffu;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
                             int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl) {
     *pl = TiledPlan{};
@@ -511,6 +562,43 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     // positions are 32-bit inside the kernels (padding included)
     if (n <= 0 || p <= 0 || nnz <= 0 || nnz + 8 * (n + p) * 4 >= (int64_t)0xfffffff0ll) return PCG_OK;
     if (n >= (int64_t)INT32_MAX || p >= (int64_t)INT32_MAX) return PCG_OK;
+    // A plan depends on the design alone (and on RG, the value type and the
+    // groups): reuse the one built for this tag when nothing it depends on has
+    // changed, the design's content included (hashed on the device: about one
+    // read of the index arrays, instead of the plan's sorts and bank order).
+    uint64_t key = 1469598103934665603ull, content = 0;
+    if (ctx->plan_cache_enabled) {
+        const uint64_t vals[] = {(uint64_t)(uintptr_t)Xr->row_ptr, (uint64_t)(uintptr_t)Xr->col_idx,
+                                 (uint64_t)(uintptr_t)Xc->col_ptr, (uint64_t)(uintptr_t)Xc->row_idx,
+                                 (uint64_t)n, (uint64_t)p, (uint64_t)nnz, (uint64_t)RG, (uint64_t)vtype,
+                                 (uint64_t)ngroups, (uint64_t)(many_products && ctx->bank_permute),
+                                 (uint64_t)ctx->num_sms};
+        for (uint64_t v : vals) key = fnv_mix(key, v);
+        for (const char *c = tag; *c; ++c) key = fnv_mix(key, (uint64_t)(unsigned char)*c);
+        cudaError_t e;
+        unsigned long long *dh = (unsigned long long *)grow(ctx, "plan:hash", sizeof(unsigned long long), &e);
+        if (!dh) return cuda_error(ctx, e, "allocating the design hash");
+        unsigned long long *hh =
+            (unsigned long long *)grow_host(ctx, "plan:hash", sizeof(unsigned long long), &e);
+        if (!hh) return cuda_error(ctx, e, "allocating the design hash");
+        PCG_CUDA_TRY(ctx, cudaMemsetAsync(dh, 0, sizeof(unsigned long long), ctx->stream));
+        k_design_hash<<<grid_for(ctx, 256, 8), 256, 0, ctx->stream>>>(Xr->row_ptr, Xr->col_idx, Xc->col_ptr,
+                                                                     Xc->row_idx, n, p, nnz, dh);
+        PCG_CUDA_TRY(ctx, cudaGetLastError());
+        PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hh, dh, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        content = *hh;
+        auto it = ctx->plan_cache.find(tag);
+        if (it != ctx->plan_cache.end() && it->second.size() == sizeof(PlanCacheEntry)) {
+            PlanCacheEntry ent;
+            memcpy(&ent, it->second.data(), sizeof ent);
+            if (ent.key == key && ent.content == content) {
+                *pl = ent.plan;
+                return PCG_OK;
+            }
+        }
+        ctx->plan_cache.erase(tag);   // rebuilt below under the same buffer names
+    }
     int64_t w = (kTileSmemBytes - RG * vsize) / (RG * vsize);   // one slot is the zero sentinel
     w = std::min<int64_t>(w, 65528);
     w &= ~int64_t(7);
@@ -564,6 +652,12 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     pl->U = grow(ctx, t + ":U", (size_t)vsize * pl->u_stride * pl->ngroups, &e);
     if (!pl->U) return cuda_error(ctx, e, "allocating the tiled u");
     pl->valid = true;
+    if (ctx->plan_cache_enabled) {
+        PlanCacheEntry ent{key, content, *pl};
+        std::vector<unsigned char> bytes(sizeof ent);
+        memcpy(bytes.data(), &ent, sizeof ent);
+        ctx->plan_cache[tag] = std::move(bytes);
+    }
     return PCG_OK;
 }
 
@@ -923,8 +1017,8 @@ __device__ __forceinline__ void chunk_add(const uint4 w, const typename Tr<T>::s
 // ln of a group reads the segment's chunks q0 + ln + G j (a group reads G
 // consecutive 16-byte chunks per load) and adds the staged values their
 // entries name; the group's lanes are summed at the end.  G (2 to 32) is
-// chosen per warp so that a typical segment of its range takes one block of
-// kBlk chunks per lane.  The warp runs in rounds of 32 / G consecutive
+// chosen per warp so that a typical segment of its range takes kRoundBlocks
+// blocks of kBlk chunks per lane.  The warp runs in rounds of 32 / G consecutive
 // segments; in a round every group runs the same number of chunks (the
 // round's longest segment: the CSR rows have similar lengths and the CSC
 // columns are stored by decreasing length), a lane past its segment's end

@@ -307,3 +307,35 @@ def test_bank_order_changes_only_rounding(pb, monkeypatch):
             assert np.array_equal(outs[0], outs[1]), prec
         else:
             assert rel(outs[0], outs[1]) < tol, prec
+
+
+def test_plan_cache_follows_the_design_content(pb):
+    """The tiled plan is built once per design and reused by later calls;
+    writing a different design (the rows permuted: same sizes and nonzero
+    count) into the same device buffers is seen by the plan's content hash,
+    the plan is rebuilt, and the draw matches the oracle for the new design."""
+    P = inputs.make_problem(4000, 500, -2.0, -1.0, seed=31, tau=0.05)
+    P.lam = np.random.default_rng(4).uniform(0.5, 2.0, P.X.p)
+    X, a = device_problem(P)
+    ctx = pb.Context(precision="fp64", profile=True)
+    args = (a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"])
+    r1 = pb.pcg_draw_beta(ctx, X, *args, tol=1e-10, max_iter=3000)
+    b1 = r1.beta.cpu().numpy()
+    r2 = pb.pcg_draw_beta(ctx, X, *args, tol=1e-10, max_iter=3000)
+    assert np.array_equal(b1, r2.beta.cpu().numpy())
+    assert pb.profile_table(ctx)["plan_bounds"][1] == 2   # one plan (two sides) for both calls
+    dense = np.zeros((P.X.n, P.X.p))
+    for j in range(P.X.p):
+        dense[P.X.row_idx[P.X.col_ptr[j]:P.X.col_ptr[j + 1]], j] = 1.0
+    X2 = inputs.design_from_dense(dense[np.random.default_rng(5).permutation(P.X.n)])
+    assert X2.nnz == P.X.nnz
+    X.row_ptr.copy_(torch.from_numpy(X2.row_ptr))
+    X.col_idx.copy_(torch.from_numpy(X2.col_idx))
+    X.col_ptr.copy_(torch.from_numpy(X2.col_ptr))
+    X.row_idx.copy_(torch.from_numpy(X2.row_idx))
+    r3 = pb.pcg_draw_beta(ctx, X, *args, tol=1e-10, max_iter=3000)
+    assert pb.profile_table(ctx)["plan_bounds"][1] == 4   # rebuilt for the new content
+    ref = O.draw_beta_cg(X2, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-10)[0]
+    b3 = r3.beta.cpu().numpy()
+    assert rel(b3, ref) < 1e-9
+    assert rel(b3, b1) > 1e-3
