@@ -116,8 +116,13 @@ typedef struct pcg_options {
 pcg_status pcg_options_default(pcg_options *opt);
 
 /* Creates a context bound to the current CUDA device and to `stream`.  The
- * context owns its workspace (grown on demand, freed by pcg_ctx_destroy) and
- * its cached graphs.  A context must not be used by two host threads at once. */
+ * context owns its workspace (grown on demand, freed by pcg_ctx_destroy), its
+ * cached graphs and its cached product plans: the tiled products' plan (tile
+ * offsets, work split, bank order) depends on X alone, so it is built on the
+ * first call for a design and reused while the design's pointers, sizes and
+ * index contents are unchanged (each call hashes the four index arrays on the
+ * device; a different design in the same buffers rebuilds the plan).  A context
+ * must not be used by two host threads at once. */
 pcg_status pcg_ctx_create(pcg_ctx **ctx, const pcg_options *opt, void *stream);
 void pcg_ctx_destroy(pcg_ctx *ctx);
 const char *pcg_last_error(const pcg_ctx *ctx);
