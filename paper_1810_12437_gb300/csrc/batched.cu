@@ -54,6 +54,8 @@ struct BatchWs {
     void *u;                                     // n*RP doubles (w64, then u32 / u64)
     double *om64;                                // n*RP
     float *om32;                                 // n*RP floats, or n*RP float pairs (df)
+    float *s_tail, *om_tail;                     // the tail plan's chain (slot 0): s (p) and omega (n),
+                                                 // contiguous, in the s32 / om32 element type
     double *partials;                            // kMaxReduceBlocks * 32
     unsigned int *counters;                      // 16
     CgScalars *sc;                               // 32
@@ -415,7 +417,9 @@ __global__ void __launch_bounds__(256) k_b_fin(const BatchDesc *__restrict__ d, 
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (p << lg2);
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = (q >> lg2) * RP + r;
-        const PT acc = sum_strided(Pc + t, T_r, (size_t)total);
+        // the tail plan's partials are one chain's, contiguous: [T_tail][p]
+        const PT acc = tail ? (r == 0 ? sum_strided(Pc + (q >> lg2), T_r, (size_t)p) : PT{})
+                            : sum_strided(Pc + t, T_r, (size_t)total);
         const double s = ws.s64[t];
         const double v = part_to_double(acc) + ws.dg[t] * s;
         ws.v64[t] = v;
@@ -638,6 +642,7 @@ __global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d,
     if (r >= d->R || ws.sc[r].done) return;
     const double gamma = ws.sc[r].gamma;
     const bool df = d->df != 0;
+    const bool tail = ws.flags[6] != 0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (d->p << lg2);
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = (q >> lg2) * RP + r;
@@ -645,6 +650,10 @@ __global__ void __launch_bounds__(256) k_b_sdir(const BatchDesc *__restrict__ d,
         ws.s64[t] = s;
         if (df) reinterpret_cast<float2 *>(ws.s32)[t] = df_from_double(s);
         else ws.s32[t] = (float)s;
+        if (tail && r == 0) {   // the tail plan gathers a contiguous copy
+            if (df) reinterpret_cast<float2 *>(ws.s_tail)[q >> lg2] = df_from_double(s);
+            else ws.s_tail[q >> lg2] = (float)s;
+        }
     }
 }
 
@@ -715,6 +724,7 @@ __global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__rest
     if (threadIdx.x < RP) perm[threadIdx.x] = ws.flags[64 + threadIdx.x];
     __syncthreads();
     const int64_t p = d->p, n = d->n;
+    const bool tail = ws.flags[6] != 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         const size_t o = (size_t)j * RP;
@@ -726,6 +736,10 @@ __global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__rest
         permute_row<RP>(ws.dg + o, perm);
         if (d->df) permute_row<RP>(reinterpret_cast<float2 *>(ws.s32) + o, perm);
         else permute_row<RP>(ws.s32 + o, perm);
+        if (tail) {   // the tail plan's chain now sits in slot 0
+            if (d->df) reinterpret_cast<float2 *>(ws.s_tail)[j] = reinterpret_cast<const float2 *>(ws.s32)[o];
+            else ws.s_tail[j] = ws.s32[o];
+        }
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -733,6 +747,10 @@ __global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__rest
         if (d->df) permute_row<RP>(reinterpret_cast<float2 *>(ws.om32) + o, perm);
         else permute_row<RP>(ws.om32 + o, perm);
         permute_row<RP>(ws.om64 + o, perm);
+        if (tail) {
+            if (d->df) reinterpret_cast<float2 *>(ws.om_tail)[i] = reinterpret_cast<const float2 *>(ws.om32)[o];
+            else ws.om_tail[i] = ws.om32[o];
+        }
     }
 }
 
@@ -830,6 +848,7 @@ struct BatchNodeArgs {
     void *pc1;
     const int *gate_tail;
     int u_blocks1, T_r1;
+    const void *s_tail, *om_tail;  // the tail chain's contiguous s and omega
 };
 
 // Adds the products of one iteration to `body` after `dep`; returns the last node.
@@ -863,13 +882,13 @@ static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, in
         // the same products by the tail plan (exit at once until it takes over)
         const TiledPlan &Q = bp.plan1;
         cudaGraphNode_t t1, tu, t2;
-        void *b1[] = {&A.ta1, &A.s_src, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        void *b1[] = {&A.ta1, &A.s_tail, &A.one, &A.zero, &A.gate_tail, &A.zero};
         e = add_node(body, &t1, &prev, 1, bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), Q.threads, b1, Q.smem_c);
         if (e != cudaSuccess) return e;
-        void *bu[] = {&A.ta1, &A.om_src, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        void *bu[] = {&A.ta1, &A.om_tail, &A.one, &A.zero, &A.gate_tail, &A.zero};
         e = add_node(body, &tu, &t1, 1, bp.tk1.u, dim3(A.u_blocks1, 1), 256, bu);
         if (e != cudaSuccess) return e;
-        void *b2[] = {&A.ta1, &A.pc1, &A.RPv, &A.zero, &A.gate_tail, &A.zero};
+        void *b2[] = {&A.ta1, &A.pc1, &A.one, &A.zero, &A.gate_tail, &A.zero};
         e = add_node(body, &t2, &tu, 1, bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), Q.threads, b2, Q.smem_r);
         if (e != cudaSuccess) return e;
         prev = t2;
@@ -910,6 +929,8 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
     A.ta1.plan = bp.plan1;
     A.pc1 = bp.tail ? bp.pc1 : bp.pc_all;
     A.gate_tail = ws.flags + 7;
+    A.s_tail = ws.s_tail;
+    A.om_tail = ws.om_tail;
     A.u_blocks1 = bp.tail ? tiled_u_blocks(bp.plan1, ctx->num_sms) : 1;
     A.T_r1 = bp.tail ? bp.plan1.T_r : bp.plan.T_r;
     cudaGraph_t g = nullptr;
@@ -1018,9 +1039,11 @@ static void launch_batch_plain_iter(pcg_ctx *ctx, const BatchWs &ws, bool refine
             const TiledPlan &Q = bp.plan1;
             TiledArgs ta1{Q};
             const int *gt = flags + 7;
-            void *b1[] = {&ta1, (void *)&s32, &rp, &zero, (void *)&gt, &zero};
-            void *bu[] = {&ta1, (void *)&om32, &rp, &zero, (void *)&gt, &zero};
-            void *b2[] = {&ta1, &pc1, &rp, &zero, (void *)&gt, &zero};
+            const void *stl = ws.s_tail, *omt = ws.om_tail;
+            int one = 1;
+            void *b1[] = {&ta1, (void *)&stl, &one, &zero, (void *)&gt, &zero};
+            void *bu[] = {&ta1, (void *)&omt, &one, &zero, (void *)&gt, &zero};
+            void *b2[] = {&ta1, &pc1, &one, &zero, (void *)&gt, &zero};
             PCG_PROF(ctx, bp.fx ? "bt1_csr_fx64" : bp.df ? "bt1_csr_df32" : "bt1_csr_f32",
                      cudaLaunchKernel(bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), dim3(Q.threads), b1, Q.smem_c, st));
             PCG_PROF(ctx, "bt1_u", cudaLaunchKernel(bp.tk1.u, dim3(tiled_u_blocks(Q, ctx->num_sms), 1), dim3(256), bu, 0, st));
@@ -1266,7 +1289,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
     // one block for the p-sized vectors and the small state
-    const size_t total_p = 7 * up(vp) + up(sizeof(float2) * (size_t)p * RP) +
+    const size_t total_p = 7 * up(vp) + up(sizeof(float2) * (size_t)p * RP) + up(sizeof(float2) * (size_t)p) +
                            up(sizeof(double) * kMaxReduceBlocks * 32) + up(64 * sizeof(unsigned)) +
                            up(sizeof(CgScalars) * kMaxBatch) + up(sizeof(int) * kFlagInts) + up(sizeof(BatchDesc));
     cudaError_t e;
@@ -1278,6 +1301,8 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     if (!bom64) return cuda_error(ctx, e, "allocating the batched workspace");
     float *bom32 = (float *)grow(ctx, "batch_om32", sizeof(float2) * (size_t)n * RP, &e);
     if (!bom32) return cuda_error(ctx, e, "allocating the batched workspace");
+    float *bomt = (float *)grow(ctx, "batch_omtail", sizeof(float2) * (size_t)n, &e);
+    if (!bomt) return cuda_error(ctx, e, "allocating the batched workspace");
     BatchWs ws{};
     size_t off = 0;
     auto take = [&](size_t sz) { char *q = bp_mem + off; off += up(sz); return q; };
@@ -1289,6 +1314,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     ws.m = (double *)take(vp);
     ws.dg = (double *)take(vp);
     ws.s32 = (float *)take(sizeof(float2) * (size_t)p * RP);
+    ws.s_tail = (float *)take(sizeof(float2) * (size_t)p);
     ws.partials = (double *)take(sizeof(double) * kMaxReduceBlocks * 32);
     ws.counters = (unsigned *)take(64 * sizeof(unsigned));
     ws.sc = (CgScalars *)take(sizeof(CgScalars) * kMaxBatch);
@@ -1297,6 +1323,7 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     ws.u = bu;
     ws.om64 = bom64;
     ws.om32 = bom32;
+    ws.om_tail = bomt;
     // counters must start at zero; the rest is written before it is read
     PCG_CUDA_TRY(ctx, cudaMemsetAsync(ws.counters, 0, 64 * sizeof(unsigned), ctx->stream));
 
