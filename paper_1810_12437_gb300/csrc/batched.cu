@@ -754,6 +754,13 @@ __global__ void __launch_bounds__(256) k_b_compact_apply(const BatchDesc *__rest
     }
 }
 
+// Graph mode with a tail plan: picks this iteration's products (the tail
+// plan's once one chain is left, else the main plan's) for the if/else node
+// that follows.
+__global__ void k_b_tail_cond(const int *__restrict__ flags, cudaGraphConditionalHandle h_tail) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_tail, flags[6] ? 1u : 0u);
+}
+
 // interleaved beta -> caller's chain-major beta
 __global__ void k_b_out(const BatchDesc *__restrict__ d, const double *__restrict__ beta,
                         const int *__restrict__ flags) {
@@ -836,7 +843,7 @@ struct BatchNodeArgs {
     const double *beta;
     const int *flag0;
     const int *flags;
-    cudaGraphConditionalHandle h_while, h_ru;
+    cudaGraphConditionalHandle h_while, h_ru, h_tail;
     int one, zero, use_ru, RPv, T_r;
     TiledArgs ta;
     void *pc_all;
@@ -865,34 +872,58 @@ static cudaError_t add_products(cudaGraph_t body, const cudaGraphNode_t *dep, in
         return add_node(body, last, &n1, 1, K.csc, grid, 256, a2);
     }
     const TiledPlan &P = bp.plan;
-    // every RHS group in one launch (blockIdx.y); finished groups exit at once
-    cudaGraphNode_t nc, prev;
-    void *a1[] = {&A.ta, &A.s_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
-    e = add_node(body, &nc, dep, dep ? ndep : 0, bp.tk.csr, dim3(P.T_c * P.csr_blocks, RP / bp.RG), P.threads, a1,
-                 P.smem_c);
-    if (e != cudaSuccess) return e;
-    cudaGraphNode_t nu;
-    void *au[] = {&A.ta, &A.om_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
-    e = add_node(body, &nu, &nc, 1, bp.tk.u, dim3(A.u_blocks, RP / bp.RG), 256, au);
-    if (e != cudaSuccess) return e;
-    void *a2[] = {&A.ta, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
-    e = add_node(body, &prev, &nu, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2, P.smem_r);
-    if (e != cudaSuccess) return e;
-    if (bp.tail) {
-        // the same products by the tail plan (exit at once until it takes over)
+    // the main plan's products: every RHS group in one launch (blockIdx.y);
+    // finished groups exit at once
+    auto add_main = [&](cudaGraph_t gph, const cudaGraphNode_t *d0, int nd0, cudaGraphNode_t *out) {
+        cudaGraphNode_t nc, nu;
+        void *a1[] = {&A.ta, &A.s_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+        cudaError_t r = add_node(gph, &nc, d0, d0 ? nd0 : 0, bp.tk.csr, dim3(P.T_c * P.csr_blocks, RP / bp.RG),
+                                 P.threads, a1, P.smem_c);
+        if (r != cudaSuccess) return r;
+        void *au[] = {&A.ta, &A.om_src, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+        r = add_node(gph, &nu, &nc, 1, bp.tk.u, dim3(A.u_blocks, RP / bp.RG), 256, au);
+        if (r != cudaSuccess) return r;
+        void *a2[] = {&A.ta, &A.pc_all, &A.RPv, &A.zero, &A.gate_base, &A.zero};
+        return add_node(gph, out, &nu, 1, bp.tk.csc, dim3(P.T_r * P.csc_chunks, RP / bp.RG), P.threads, a2,
+                        P.smem_r);
+    };
+    // the tail plan's products (group width 1, the chain in slot 0)
+    auto add_tail = [&](cudaGraph_t gph, const cudaGraphNode_t *d0, int nd0, cudaGraphNode_t *out) {
         const TiledPlan &Q = bp.plan1;
-        cudaGraphNode_t t1, tu, t2;
+        cudaGraphNode_t t1, tu;
         void *b1[] = {&A.ta1, &A.s_tail, &A.one, &A.zero, &A.gate_tail, &A.zero};
-        e = add_node(body, &t1, &prev, 1, bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), Q.threads, b1, Q.smem_c);
-        if (e != cudaSuccess) return e;
+        cudaError_t r = add_node(gph, &t1, d0, d0 ? nd0 : 0, bp.tk1.csr, dim3(Q.T_c * Q.csr_blocks, 1), Q.threads,
+                                 b1, Q.smem_c);
+        if (r != cudaSuccess) return r;
         void *bu[] = {&A.ta1, &A.om_tail, &A.one, &A.zero, &A.gate_tail, &A.zero};
-        e = add_node(body, &tu, &t1, 1, bp.tk1.u, dim3(A.u_blocks1, 1), 256, bu);
-        if (e != cudaSuccess) return e;
+        r = add_node(gph, &tu, &t1, 1, bp.tk1.u, dim3(A.u_blocks1, 1), 256, bu);
+        if (r != cudaSuccess) return r;
         void *b2[] = {&A.ta1, &A.pc1, &A.one, &A.zero, &A.gate_tail, &A.zero};
-        e = add_node(body, &t2, &tu, 1, bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), Q.threads, b2, Q.smem_r);
+        return add_node(gph, out, &tu, 1, bp.tk1.csc, dim3(Q.T_r * Q.csc_chunks, 1), Q.threads, b2, Q.smem_r);
+    };
+    cudaGraphNode_t prev;
+    if (!bp.tail) {
+        e = add_main(body, dep, ndep, &prev);
+    } else {
+        // one set of products per iteration: an if/else node on the tail flag
+        // (set by a one-thread kernel), so the plan not in use launches nothing
+        cudaGraphNode_t nsel;
+        void *as[] = {&A.flags, &A.h_tail};
+        e = add_node(body, &nsel, dep, dep ? ndep : 0, (void *)k_b_tail_cond, dim3(1), 32, as);
         if (e != cudaSuccess) return e;
-        prev = t2;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = A.h_tail;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 2;   // [0]: taken when the value is nonzero, [1]: otherwise
+        e = cudaGraphAddNode(&prev, body, &nsel, nullptr, 1, &cp);
+        if (e != cudaSuccess) return e;
+        cudaGraphNode_t last_t, last_m;
+        e = add_tail(cp.conditional.phGraph_out[0], nullptr, 0, &last_t);
+        if (e != cudaSuccess) return e;
+        e = add_main(cp.conditional.phGraph_out[1], nullptr, 0, &last_m);
     }
+    if (e != cudaSuccess) return e;
     void *a3[] = {&A.d, &A.pc_all, &A.T_r, &A.pc1, &A.T_r1, &A.ws};
     return add_node(body, last, &prev, 1, K.fin, gvec, 256, a3);
 }
@@ -956,6 +987,7 @@ static pcg_status build_batch_graph(pcg_ctx *ctx, const BatchWs &ws, int RP, boo
         e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
         if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
+    if (e == cudaSuccess && bp.tail) e = cudaGraphConditionalHandleCreate(&A.h_tail, body, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) e = add_products(body, nullptr, 0, A, K, bp, RP, grid, gvec, &n_prod);
     if (e == cudaSuccess && refined) e = cudaGraphConditionalHandleCreate(&A.h_ru, body, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
@@ -1141,11 +1173,12 @@ static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool ref
         PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hflags, ws.flags, sizeof(int) * kFlagInts, cudaMemcpyDeviceToHost, ctx->stream));
         PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         // graph nodes that ran: prep, init and the output transpose; per loop
-        // trip (at least one) the products, update and direction; 2 per
-        // float64 recomputation of r
+        // trip (at least one) the products (one plan's three; with a tail plan
+        // also the kernel that picks the plan), the finalize, update, direction
+        // and compaction; 2 per float64 recomputation of r
         int trips = 1;
         for (int r = 0; r < nrhs; ++r) trips = std::max(trips, hsc[r].iter);
-        const int per_trip = (bp.RG ? 3 + (bp.tail ? 3 : 0) + 1 + 2 : 2) + 2;
+        const int per_trip = (bp.RG ? 3 + (bp.tail ? 1 : 0) + 1 + 2 : 2) + 2;
         ctx->last_launches += 3 + (int64_t)per_trip * trips + 2 * (int64_t)hflags[2];
         return PCG_OK;
     }
