@@ -127,6 +127,28 @@ pcg_status pcg_ctx_create(pcg_ctx **ctx, const pcg_options *opt, void *stream);
 void pcg_ctx_destroy(pcg_ctx *ctx);
 const char *pcg_last_error(const pcg_ctx *ctx);
 
+/*
+ * Unshrunk coefficients (Sec. S4.3): coefficients 0 .. q1-1 (an intercept,
+ * predictors of interest) take independent Gaussian priors N(0, sigma_j^2)
+ * instead of the shrinkage prior, so that
+ *     Phi = X^T Omega X + diag(sigma_0^-2 .. sigma_{q1-1}^-2, tau^-2 lambda_q1^-2 ..),
+ * the prior term of Eq. 2.3 is sigma_j^-1 delta_j for them, and the CG
+ * preconditioner is M = diag(gamma^-2, tau^-2 Lambda^-2) with the scales
+ * gamma_j of Sec. S4.3 (c times an estimate of the posterior standard
+ * deviation of beta_j, c >= 1); the stop rule's norm ||M^-1/2 r|| uses that M.
+ * prior_prec: device, q1 entries sigma_j^-2 >= 0 (0: the flat prior of an
+ * uninformative coefficient); precond_scale: device, q1 entries gamma_j > 0.
+ * Both are copied into the context (the caller keeps ownership) and apply to
+ * the later pcg_draw_beta, pcg_solve, pcg_draw_beta_batched (every chain),
+ * pcg_build_rhs and pcg_phi_mul calls on this context, where lambda[j] is
+ * then not read for j < q1; q1 = 0 switches them off.  PCG_BADARG for q1 < 0,
+ * NULL vectors, a negative or non-finite precision or a non-positive or
+ * non-finite gamma (the setting is then cleared), for a later call whose X has
+ * fewer than q1 columns, and for pcg_draw_beta_uneven and pcg_adjoint while
+ * set (their tau and lambda derivatives assume the shrinkage prior throughout).
+ */
+pcg_status pcg_set_unshrunk(pcg_ctx *ctx, int q1, const double *prior_prec, const double *precond_scale);
+
 /* Checks on the device that csr and csc are valid, agree in n, p and nnz and
  * hold the same set of (i, j) entries; never dereferences a stored index.
  * Returns PCG_OK or PCG_BADARG. */

@@ -12,7 +12,11 @@ Eq. 2.4):
                         triangular solves (Sec. 1);
 * ``adjoint``        -- gradient of L = c^T beta, by implicit differentiation
                         of beta = Phi^-1 b (not in the paper; derivation in
-                        the docstring).
+                        the docstring);
+* ``*_unshrunk``     -- the same draw with unshrunk coefficients (Sec. S4.3):
+                        their own prior precisions in Phi and Eq. 2.3 and
+                        separate preconditioner scales (plain numpy, small
+                        cases).
 
 Every function takes the same numpy inputs as the CUDA path (see
 ``paper_1810_12437_gb300.inputs``).  Parity: each routine is pinned by the
@@ -252,3 +256,88 @@ def adjoint_cg(X, omega, z, lam, tau, eta, delta, c, *, tol=1e-12, stop_rule=STO
     beta = pcg(X, omega, lam, tau, b, tol=tol, stop_rule=stop_rule, max_iter=max_iter)[0]
     g = pcg(X, omega, lam, tau, c, tol=tol, stop_rule=stop_rule, max_iter=max_iter)[0]
     return beta, adjoint_from_g(X, omega, z, lam, tau, eta, delta, beta, g, mode)
+
+
+# ---------------------------------------------------------------------------
+# Unshrunk coefficients (Sec. S4.3).  Coefficients 0 .. q1-1 take independent
+# priors N(0, sigma_j^2) (sigma_j = infinity, precision 0, for a flat prior)
+# instead of the shrinkage prior, so Phi's diagonal prior term is sigma_j^-2
+# for them; the preconditioner uses separate scales gamma_j, M = diag(gamma^-2,
+# tau^-2 Lambda^-2).  Plain numpy on the dense design: for small cases only.
+# ---------------------------------------------------------------------------
+def prior_terms_unshrunk(lam, tau, prior_prec, gamma):
+    """Per coefficient: prior precision d, its square root (the prior term of
+    Eq. 2.3, sigma_j^-1 delta_j for the unshrunk ones) and the preconditioner
+    variance m = M^-1 (gamma_j^2 for the unshrunk ones, tau^2 lambda_j^2 after)."""
+    lam = _f64(lam)
+    prior_prec = np.asarray(prior_prec, dtype=np.float64)
+    q1 = prior_prec.size
+    d = 1.0 / (tau * lam) ** 2
+    sd = 1.0 / (tau * lam)
+    m = (tau * lam) ** 2
+    d[:q1] = prior_prec
+    sd[:q1] = np.sqrt(prior_prec)
+    if gamma is not None:
+        m[:q1] = np.asarray(gamma, dtype=np.float64) ** 2
+    return d, sd, m
+
+
+def build_b_unshrunk(X, omega, z, lam, tau, eta, delta, prior_prec):
+    """Eq. 2.3 with the prior of Sec. S4.3: b = X^T Omega z + X^T Omega^1/2 eta
+    + diag(d)^1/2 delta, d the prior precision of each coefficient."""
+    omega, z, eta, delta = map(_f64, (omega, z, eta, delta))
+    _, sd, _ = prior_terms_unshrunk(lam, tau, prior_prec, None)
+    xd = X.dense()
+    return xd.T @ (omega * z + np.sqrt(omega) * eta) + sd * delta
+
+
+def dense_phi_unshrunk(X, omega, lam, tau, prior_prec):
+    """Phi of Sec. S4.3: X^T Omega X + diag(sigma^-2 (unshrunk), tau^-2 lambda^-2)."""
+    d, _, _ = prior_terms_unshrunk(lam, tau, prior_prec, None)
+    xd = X.dense()
+    return xd.T @ (_f64(omega)[:, None] * xd) + np.diag(d)
+
+
+def draw_beta_chol_unshrunk(X, omega, z, lam, tau, eta, delta, prior_prec):
+    """Direct draw with unshrunk coefficients: b as above, beta = Phi^-1 b
+    (numpy Cholesky)."""
+    b = build_b_unshrunk(X, omega, z, lam, tau, eta, delta, prior_prec)
+    l = np.linalg.cholesky(dense_phi_unshrunk(X, omega, lam, tau, prior_prec))
+    return np.linalg.solve(l.T, np.linalg.solve(l, b))
+
+
+def pcg_unshrunk(X, omega, lam, tau, b, prior_prec, gamma, *, tol=1e-6, stop_rule=STOP_RMS,
+                 max_iter=10_000):
+    """PCG from beta_0 = 0 (Algorithm S1 in PCG form) on Phi of Sec. S4.3 with
+    M^-1 = diag(gamma^2, tau^2 Lambda^2); stop rule Eq. S2 on rho = r . (M^-1 r).
+    Returns (beta, iters, resid, status)."""
+    omega, b = _f64(omega), _f64(b)
+    d, _, m = prior_terms_unshrunk(lam, tau, prior_prec, gamma)
+    p = b.size
+    beta = np.zeros(p)
+    r = b.copy()
+    zz = m * r
+    s = zz.copy()
+    rho = float(r @ zz)
+    rho0 = rho
+
+    def resid(rh):
+        return np.sqrt(rh / p) if stop_rule == STOP_RMS else np.sqrt(rh / rho0)
+
+    if resid(rho) <= tol:
+        return beta, 0, resid(rho), OK
+    for k in range(1, max_iter + 1):
+        v = xt_mul(X, omega * x_mul(X, s)) + d * s
+        sigma = float(s @ v)
+        if not (sigma > 0.0):
+            return beta, k, resid(rho), BREAKDOWN
+        alpha = rho / sigma
+        beta = beta + alpha * s
+        r = r - alpha * v
+        zz = m * r
+        rho_new = float(r @ zz)
+        if resid(rho_new) <= tol:
+            return beta, k, resid(rho_new), OK
+        s = zz + (rho_new / rho) * s
+        rho = rho_new
+    return beta, max_iter, resid(rho), MAXITER

@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
             "pcg_ctx_destroy": ([P], None),
             "pcg_last_error": ([P], ctypes.c_char_p),
             "pcg_check_design": ([P, pCsr, pCsc], I),
+            "pcg_set_unshrunk": ([P, I, P, P], I),
             "pcg_build_rhs": ([P, pCsc, P, P, P, D, P, P, P], I),
             "pcg_phi_mul": ([P, pCsr, pCsc, P, P, D, P, P], I),
             "pcg_draw_beta": ([P, pCsr, pCsc, P, P, P, D, P, P, D, I, P, pI, pD], I),
@@ -107,7 +108,7 @@ def exported_symbols() -> Sequence[str]:
             "pcg_check_design", "pcg_build_rhs", "pcg_phi_mul", "pcg_draw_beta", "pcg_solve",
             "pcg_draw_beta_batched", "pcg_draw_beta_uneven", "pcg_adjoint", "pcg_profile_count",
             "pcg_profile_entry", "pcg_profile_reset", "pcg_last_kernel_launches",
-            "pcg_phi_mul_noalloc"]
+            "pcg_phi_mul_noalloc", "pcg_set_unshrunk"]
 
 
 # ---------------------------------------------------------------------------
@@ -242,6 +243,23 @@ def pcg_check_design(ctx: Context, X: DeviceDesign) -> int:
     with torch.cuda.device(ctx.device):
         return ctx.check(ctx._lib.pcg_check_design(ctx.handle, ctypes.byref(csr), ctypes.byref(csc)),
                          fatal=(PCG_TIMEOUT, PCG_CUDA))
+
+
+def pcg_set_unshrunk(ctx: Context, prior_prec=None, precond_scale=None) -> None:
+    """Coefficients 0 .. q1-1 unshrunk (Sec. S4.3): prior precisions
+    sigma_j^-2 (>= 0; 0 = flat prior) and preconditioner scales gamma_j (> 0),
+    float64 device tensors of q1 entries each; None (or q1 = 0) clears."""
+    f = torch.float64
+    if prior_prec is None or prior_prec.numel() == 0:
+        with torch.cuda.device(ctx.device):
+            ctx.check(ctx._lib.pcg_set_unshrunk(ctx.handle, 0, None, None))
+        return
+    q1 = int(prior_prec.numel())
+    dev = prior_prec.device
+    _dev(prior_prec, f, q1, "prior_prec", dev)
+    _dev(precond_scale, f, q1, "precond_scale", dev)
+    with torch.cuda.device(ctx.device):
+        ctx.check(ctx._lib.pcg_set_unshrunk(ctx.handle, q1, _ptr(prior_prec), _ptr(precond_scale)))
 
 
 def pcg_build_rhs(ctx, X, omega, z, lam, tau, eta, delta, out=None):

@@ -37,6 +37,10 @@ struct BatchDesc {
     int RG;   // right-hand sides per tiled product group (0: untiled products)
     int df;   // double-float products: s32 / om32 hold float pairs (float2)
     int tail; // a group-width-1 plan takes over the products when one chain is left
+    // unshrunk coefficients 0 .. q1-1 of every chain (Sec. S4.3): prior precision
+    // ud[j] (0: flat prior) and preconditioner variance um[j] = gamma_j^2
+    int q1;
+    const double *ud, *um;
 };
 
 // flags[] layout (kFlagInts ints, device):
@@ -223,9 +227,11 @@ __global__ void __launch_bounds__(256) k_b_init(const BatchDesc *__restrict__ d,
                 double b = 0.0, m = 0.0, dg = 0.0;
                 if (r < R) {
                     const double tau = d->tau[r], lam = d->lambda[(size_t)r * p + j];
-                    b = a[q] + d->delta[(size_t)r * p + j] / (tau * lam);
-                    m = prior_var(tau, lam);
-                    dg = prior_prec(tau, lam);
+                    const bool un = j < d->q1;   // unshrunk coefficient
+                    dg = un ? d->ud[j] : prior_prec(tau, lam);
+                    m = un ? d->um[j] : prior_var(tau, lam);
+                    const double dl = d->delta[(size_t)r * p + j];
+                    b = a[q] + (un ? dl * sqrt(dg) : dl / (tau * lam));
                 }
                 const double zz = m * b;
                 ws.b[o] = b;
@@ -1387,6 +1393,11 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     d.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
     d.df = prec_pairs(ctx->opt.precision) ? 1 : 0;
+    if (ctx->unshrunk_q1 > Xr->p)
+        return set_error(ctx, PCG_BADARG, "more unshrunk coefficients (pcg_set_unshrunk) than columns of X");
+    d.q1 = ctx->unshrunk_q1;
+    d.ud = ctx->unshrunk_d;
+    d.um = ctx->unshrunk_m;
     const bool refined = d.refined != 0;
     int RG = 0;
     pcg_status st = choose_rg(ctx, Xr, Xc, ws, d, hd, RP, refined, nrhs, hsc, hflags, &RG);

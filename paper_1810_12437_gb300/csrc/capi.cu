@@ -205,6 +205,18 @@ void prof_collect(pcg_ctx *ctx) {
 
 using namespace pcg;
 
+// um[j] = gamma_j^2 and ud[j] = prior precision; *bad = 1 if some prior
+// precision is negative or not finite, or some gamma is not positive and finite
+__global__ void k_unshrunk(const double *__restrict__ prec, const double *__restrict__ gamma, int q1,
+                           double *__restrict__ ud, double *__restrict__ um, int *__restrict__ bad) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q1; j += gridDim.x * blockDim.x) {
+        const double a = prec[j], g = gamma[j];
+        if (!(a >= 0.0) || !isfinite(a) || !(g > 0.0) || !isfinite(g)) *bad = 1;
+        ud[j] = a;
+        um[j] = g * g;
+    }
+}
+
 extern "C" {
 
 pcg_status pcg_options_default(pcg_options *opt) {
@@ -270,6 +282,39 @@ void pcg_ctx_destroy(pcg_ctx *ctx) {
 
 const char *pcg_last_error(const pcg_ctx *ctx) {
     return ctx ? ctx->last_error.c_str() : "NULL context";
+}
+
+pcg_status pcg_set_unshrunk(pcg_ctx *ctx, int q1, const double *prior_prec, const double *precond_scale) {
+    if (!ctx) return PCG_BADARG;
+    if (q1 < 0) return set_error(ctx, PCG_BADARG, "negative count of unshrunk coefficients");
+    if (q1 == 0) {
+        ctx->unshrunk_q1 = 0;
+        return PCG_OK;
+    }
+    if (!prior_prec || !precond_scale) return set_error(ctx, PCG_BADARG, "NULL vector");
+    cudaError_t e;
+    double *ud = (double *)grow(ctx, "unshrunk_d", sizeof(double) * (size_t)q1, &e);
+    if (!ud) return cuda_error(ctx, e, "allocating the unshrunk coefficients");
+    double *um = (double *)grow(ctx, "unshrunk_m", sizeof(double) * (size_t)q1, &e);
+    if (!um) return cuda_error(ctx, e, "allocating the unshrunk coefficients");
+    int *dbad = (int *)grow(ctx, "unshrunk_bad", sizeof(int), &e);
+    if (!dbad) return cuda_error(ctx, e, "allocating the unshrunk coefficients");
+    int *hbad = (int *)grow_host(ctx, "unshrunk_bad", sizeof(int), &e);
+    if (!hbad) return cuda_error(ctx, e, "allocating the unshrunk coefficients");
+    PCG_CUDA_TRY(ctx, cudaMemsetAsync(dbad, 0, sizeof(int), ctx->stream));
+    k_unshrunk<<<std::min(1024, (q1 + 255) / 256), 256, 0, ctx->stream>>>(prior_prec, precond_scale, q1, ud, um,
+                                                                         dbad);
+    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*hbad) {
+        ctx->unshrunk_q1 = 0;
+        return set_error(ctx, PCG_BADARG, "prior precisions must be >= 0 and gammas > 0, all finite");
+    }
+    ctx->unshrunk_q1 = q1;
+    ctx->unshrunk_d = ud;
+    ctx->unshrunk_m = um;
+    return PCG_OK;
 }
 
 pcg_status pcg_check_design(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc) {
@@ -392,6 +437,8 @@ pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *prob
     if (nprob < 0 || (nprob > 0 && (!probs || !iters || !resid || !status)))
         return set_error(ctx, PCG_BADARG, "bad problem list");
     if (!(tol >= 0.0) || max_iter < 0) return set_error(ctx, PCG_BADARG, "tol >= 0 and max_iter >= 0 required");
+    if (ctx->unshrunk_q1 > 0)
+        return set_error(ctx, PCG_BADARG, "the uneven batch takes no unshrunk coefficients (pcg_set_unshrunk)");
     for (int q = 0; q < nprob; ++q) {
         pcg_status st = check_shapes(ctx, &probs[q].X_csr, &probs[q].X_csc);
         if (st != PCG_OK) return st;
@@ -412,6 +459,8 @@ pcg_status pcg_adjoint(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const
                        double *g_logtau, int *iters, double *resid) {
     if (!ctx) return PCG_BADARG;
     if (mode != PCG_ADJ_SOLVE && mode != PCG_ADJ_DRAW) return set_error(ctx, PCG_BADARG, "bad adjoint mode");
+    if (ctx->unshrunk_q1 > 0)
+        return set_error(ctx, PCG_BADARG, "the adjoint takes no unshrunk coefficients (pcg_set_unshrunk)");
     if (!g_logtau || !iters || !resid) return set_error(ctx, PCG_BADARG, "NULL host output");
     *g_logtau = 0.0;
     pcg_status st = check_shapes(ctx, Xr, Xc);

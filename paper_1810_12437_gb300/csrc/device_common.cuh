@@ -92,6 +92,19 @@ __device__ __forceinline__ double prior_var(double tau, double lam) {
     return t * t;
 }
 
+// The same per coefficient of a single-RHS draw: d_j, m_j and the prior term
+// sqrt(d_j) delta_j of Eq. 2.3, with the unshrunk coefficients j < q1 (Sec. S4.3)
+// taking their prior precision sigma_j^-2 and preconditioner variance gamma_j^2.
+__device__ __forceinline__ double desc_d(const DrawDesc *d, int64_t j) {
+    return j < d->q1 ? d->ud[j] : prior_prec(d->tau, d->lambda[j]);
+}
+__device__ __forceinline__ double desc_m(const DrawDesc *d, int64_t j) {
+    return j < d->q1 ? d->um[j] : prior_var(d->tau, d->lambda[j]);
+}
+__device__ __forceinline__ double desc_prior_term(const DrawDesc *d, int64_t j, double delta) {
+    return j < d->q1 ? delta * sqrt(d->ud[j]) : delta / (d->tau * d->lambda[j]);
+}
+
 // Streaming loads of index arrays (read once per pass: keep them out of L1
 // and mark them first to evict from L2), and cached loads of gathered vectors.
 __device__ __forceinline__ int32_t ld_stream(const int32_t *p) { return __ldcs(p); }

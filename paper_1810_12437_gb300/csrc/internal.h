@@ -57,6 +57,10 @@ struct DrawDesc {
     double tau, tol;
     int max_iter, stop_rule, refined, reliable_k;
     int df;                // double-float products: keep s (and omega) as float pairs too
+    // unshrunk coefficients 0 .. q1-1 (Sec. S4.3): prior precision ud[j] = sigma_j^-2
+    // (0: flat prior) and preconditioner variance um[j] = gamma_j^2 (device, q1 each)
+    int q1;
+    const double *ud, *um;
 };
 
 // Device workspace of the single-RHS path (sizes grow on demand).
@@ -133,6 +137,9 @@ struct pcg_ctx {
     // key and design-content hash it was built for (PCG_BETA_PLAN_CACHE=0: off)
     std::map<std::string, std::vector<unsigned char>> plan_cache;
     bool plan_cache_enabled = true;
+    // unshrunk coefficients set by pcg_set_unshrunk (context-owned device copies)
+    int unshrunk_q1 = 0;
+    double *unshrunk_d = nullptr, *unshrunk_m = nullptr;
 };
 
 namespace pcg {

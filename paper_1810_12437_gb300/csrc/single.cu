@@ -78,7 +78,7 @@ __global__ void k_t_fin_out(const DrawDesc *__restrict__ d, TiledArgs A, const d
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         const T acc = sum_strided(Pc + j, P.T_r, (size_t)p);
-        out[j] = part_to_double(acc) + prior_prec(d->tau, d->lambda[j]) * v[j];
+        out[j] = part_to_double(acc) + desc_d(d, j) * v[j];
     }
 }
 
@@ -106,9 +106,8 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
             acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], w, lane);
         acc = group_sum<G>(acc);
         if (j < p && lane == 0) {
-            const double lam = d->lambda[j];
-            const double b = d->rhs ? d->rhs[j] : acc + d->delta[j] / (tau * lam);
-            const double z = prior_var(tau, lam) * b;
+            const double b = d->rhs ? d->rhs[j] : acc + desc_prior_term(d, j, d->delta[j]);
+            const double z = desc_m(d, j) * b;
             ws.b[j] = b;
             ws.r[j] = b;
             ws.s64[j] = z;
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(256) k_csc(const DrawDesc *__restrict__ d,
         acc = group_sum<G>(acc);
         if (j < p && lane == 0) {
             const double sj = sv[j];
-            const double v = (double)acc + prior_prec(tau, d->lambda[j]) * sj;
+            const double v = (double)acc + desc_d(d, j) * sj;
             out[j] = v;
             sig += sj * v;
         }
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(256) k_update(const DrawDesc *__restrict__ d, 
         const double rj = ws.r[j] - alpha * ws.v64[j];
         d->beta[j] = bj;
         ws.r[j] = rj;
-        rho += rj * (prior_var(tau, d->lambda[j]) * rj);
+        rho += rj * (desc_m(d, j) * rj);
     }
     const double tot = block_sum(rho, red);
     if (grid_reduce<1>(&tot, ws.partials, ws.counters + 2, sums, red) && threadIdx.x == 0) {
@@ -315,11 +314,10 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
             acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], u64, lane);
         acc = group_sum<G>(acc);
         if (j < p && lane == 0) {
-            const double lam = d->lambda[j];
             const double bj = d->beta[j];
-            const double rj = ws.b[j] - (acc + prior_prec(tau, lam) * bj);
+            const double rj = ws.b[j] - (acc + desc_d(d, j) * bj);
             ws.r[j] = rj;
-            rho += rj * (prior_var(tau, lam) * rj);
+            rho += rj * (desc_m(d, j) * rj);
         }
     }
     const double tot = block_sum(rho, red);
@@ -369,7 +367,7 @@ __global__ void __launch_bounds__(256) k_sdir(const DrawDesc *__restrict__ d, Si
     const double gamma = sc->gamma;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const double s = prior_var(tau, d->lambda[j]) * ws.r[j] + gamma * ws.s64[j];
+        const double s = desc_m(d, j) * ws.r[j] + gamma * ws.s64[j];
         ws.s64[j] = s;
         ws.s32[j] = (float)s;
         if (d->df) ws.sdf[j] = df_from_double(s);
@@ -406,7 +404,7 @@ __global__ void __launch_bounds__(256) k_rhs_b(const DrawDesc *__restrict__ d,
         if (j < p)
             acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], w, lane);
         acc = group_sum<G>(acc);
-        if (j < p && lane == 0) b[j] = acc + d->delta[j] / (d->tau * d->lambda[j]);
+        if (j < p && lane == 0) b[j] = acc + desc_prior_term(d, j, d->delta[j]);
     }
 }
 
@@ -776,6 +774,16 @@ static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, cons
     return PCG_OK;
 }
 
+// The context's unshrunk coefficients (pcg_set_unshrunk) into a descriptor.
+static pcg_status with_unshrunk(pcg_ctx *ctx, DrawDesc &d) {
+    if (ctx->unshrunk_q1 > d.p)
+        return set_error(ctx, PCG_BADARG, "more unshrunk coefficients (pcg_set_unshrunk) than columns of X");
+    d.q1 = ctx->unshrunk_q1;
+    d.ud = ctx->unshrunk_d;
+    d.um = ctx->unshrunk_m;
+    return PCG_OK;
+}
+
 pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode, int *iters,
                       double *resid) {
     pcg_status st = ensure_single_ws(ctx, din.n, din.p);
@@ -784,6 +792,8 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     d.refined = (precision == PCG_PREC_FP32_REFINED) ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
     d.df = prec_pairs(precision) ? 1 : 0;
+    st = with_unshrunk(ctx, d);
+    if (st != PCG_OK) return st;
     *ctx->h_desc = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
                                       cudaMemcpyHostToDevice, ctx->stream));
@@ -857,6 +867,8 @@ pcg_status launch_build_rhs(pcg_ctx *ctx, const pcg_csc *X, const double *omega,
     d.p = X->p;
     d.nnz = X->nnz;
     d.tau = tau;
+    st = with_unshrunk(ctx, d);
+    if (st != PCG_OK) return st;
     *ctx->h_desc = d;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),
                                       cudaMemcpyHostToDevice, ctx->stream));
@@ -885,6 +897,8 @@ pcg_status launch_phi_mul(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, co
     d.p = Xr->p;
     d.nnz = Xr->nnz;
     d.tau = tau;
+    st = with_unshrunk(ctx, d);
+    if (st != PCG_OK) return st;
     *ctx->h_desc = d;
     cudaStream_t s = ctx->stream;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws.desc, ctx->h_desc, sizeof(DrawDesc),

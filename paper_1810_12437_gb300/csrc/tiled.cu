@@ -1284,7 +1284,7 @@ __global__ void __launch_bounds__(256) k_t_fin1(const DrawDesc *__restrict__ d, 
          j += (int64_t)gridDim.x * blockDim.x) {
         const T acc = sum_strided(Pc + j, P.T_r, (size_t)p);
         const double sj = ws.s64[j];
-        const double v = part_to_double(acc) + prior_prec(tau, d->lambda[j]) * sj;
+        const double v = part_to_double(acc) + desc_d(d, j) * sj;
         ws.v64[j] = v;
         sig += sj * v;
     }

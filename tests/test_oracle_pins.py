@@ -381,3 +381,60 @@ def test_adjoint_symmetry_and_cg_agree_with_cholesky():
     for key in ("b", "omega", "log_lambda"):
         assert rel(gg[key], gc[key]) < 1e-8, key
     assert gg["log_tau"] == pytest.approx(gc["log_tau"], rel=1e-8)
+
+
+# --------------------------------------------------------------------------
+# unshrunk coefficients (Sec. S4.3)
+# --------------------------------------------------------------------------
+def test_unshrunk_reduces_to_shrunk_when_scales_match():
+    """Sec. S4.3 with sigma_j^-2 = tau^-2 lambda_j^-2 and gamma_j = tau lambda_j
+    is the shrinkage model: the draw, the right-hand side and the CG path (its
+    iteration count) equal the C oracle's."""
+    P = small_problem(n=80, p=24, seed=11)
+    q1 = 5
+    prec = 1.0 / (P.tau * P.lam[:q1]) ** 2
+    gam = P.tau * P.lam[:q1]
+    b = O.build_b_unshrunk(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, prec)
+    assert rel(b, O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)) < 1e-13
+    beta = O.draw_beta_chol_unshrunk(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, prec)
+    assert rel(beta, O.draw_beta_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)) < 1e-11
+    ref, k, _, _ = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10)
+    got, k2, _, st = O.pcg_unshrunk(P.X, P.omega, P.lam, P.tau, b, prec, gam, tol=1e-10)
+    assert st == O.OK and k2 == k and rel(got, ref) < 1e-10
+
+
+def test_unshrunk_flat_prior_intercept_closed_form():
+    """An intercept-only model (X a column of ones) under the flat prior of
+    Sec. S4.3 (sigma = infinity): Phi = sum_i omega_i and
+    b = sum_i (omega_i z_i + omega_i^1/2 eta_i), so beta = b / Phi."""
+    rng = np.random.default_rng(3)
+    n = 500
+    X = inputs.design_from_dense(np.ones((n, 1)))
+    om = rng.uniform(0.05, 0.25, n)
+    z = rng.standard_normal(n) / om
+    eta = rng.standard_normal(n)
+    want = (om @ z + np.sqrt(om) @ eta) / om.sum()
+    lam, delta = np.ones(1), rng.standard_normal(1)   # lambda, delta unused for an unshrunk flat coefficient
+    got = O.draw_beta_chol_unshrunk(X, om, z, lam, 0.1, eta, delta, [0.0])
+    assert abs(got[0] - want) <= 1e-12 * abs(want)
+    b = O.build_b_unshrunk(X, om, z, lam, 0.1, eta, delta, [0.0])
+    beta, k, _, st = O.pcg_unshrunk(X, om, lam, 0.1, b, [0.0], [1.0], tol=1e-12)
+    assert st == O.OK and k == 1 and abs(beta[0] - want) <= 1e-12 * abs(want)
+
+
+def test_unshrunk_cg_matches_cholesky_and_ignores_gamma():
+    """With an intercept column, a flat and two proper unshrunk priors: the
+    PCG solution equals the Cholesky draw, and the preconditioner scales gamma
+    (Sec. S4.3) change the path but not the solution."""
+    P = small_problem(n=120, p=30, seed=5)
+    dense = P.X.dense()
+    dense[:, 0] = 1.0
+    P.X = inputs.design_from_dense(dense)
+    prec = np.array([0.0, 0.01, 4.0])
+    ref = O.draw_beta_chol_unshrunk(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, prec)
+    b = O.build_b_unshrunk(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, prec)
+    for gam in ([1.0, 1.0, 1.0], [100.0, 0.01, 3.0]):
+        beta, k, _, st = O.pcg_unshrunk(P.X, P.omega, P.lam, P.tau, b, prec, gam, tol=1e-12,
+                                        stop_rule=O.STOP_RELATIVE)
+        assert st == O.OK
+        assert rel(beta, ref) < 1e-9
