@@ -1157,7 +1157,6 @@ static pcg_status make_products(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *
 static pcg_status batched_once(pcg_ctx *ctx, const BatchWs &ws, int RP, bool refined, int nrhs,
                                int max_iter, const BatchProducts &bp, CgScalars *hsc, int *hflags) {
     const int grid = grid_for(ctx, 256, 8), gvec = grid_for(ctx, 256, 4);
-    cudaError_t e;
     if (ctx->opt.use_graph && !ctx->opt.profile) {
         char key[256];
         snprintf(key, sizeof key, "batch:%d:%d:%d:%d:%p:%p:%p:%p:%p|%d%s%s:%016llx:%016llx:%p:%p",

@@ -92,7 +92,6 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
     __shared__ double red[32];
     __shared__ double sums[1];
     const int64_t p = d->p;
-    const double tau = d->tau;
     const int lane = threadIdx.x & (G - 1);
     const int64_t gpw = 32 / G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -189,7 +188,6 @@ __global__ void __launch_bounds__(256) k_csc(const DrawDesc *__restrict__ d,
     __shared__ double sums[1];
     if (reduce && *(volatile const int *)&ws.sc->done) return;
     const int64_t p = d->p;
-    const double tau = d->tau;
     const int lane = threadIdx.x & (G - 1);
     const int64_t gpw = 32 / G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -240,7 +238,6 @@ __global__ void __launch_bounds__(256) k_update(const DrawDesc *__restrict__ d, 
         return;
     }
     const int64_t p = d->p;
-    const double tau = d->tau;
     const double alpha = sc->alpha;
     double rho = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
@@ -300,7 +297,6 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
     CgScalars *sc = ws.sc;
     if (gated && gate_closed(&sc->done, &sc->need_ru)) return;
     const int64_t p = d->p;
-    const double tau = d->tau;
     const int lane = threadIdx.x & (G - 1);
     const int64_t gpw = 32 / G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -363,7 +359,6 @@ __global__ void __launch_bounds__(256) k_sdir(const DrawDesc *__restrict__ d, Si
         cudaGraphSetConditional(h_while, done ? 0u : 1u);
     if (done) return;
     const int64_t p = d->p;
-    const double tau = d->tau;
     const double gamma = sc->gamma;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -448,11 +443,6 @@ static void *rhs_init_ptr(int G) {
 static void *true_resid_ptr(int G) {
     void *f = nullptr;
     PCG_DISPATCH_G(G, f = (void *)k_true_resid<GG>);
-    return f;
-}
-static void *rhs_b_ptr(int G) {
-    void *f = nullptr;
-    PCG_DISPATCH_G(G, f = (void *)k_rhs_b<GG>);
     return f;
 }
 
