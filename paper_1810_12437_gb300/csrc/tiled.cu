@@ -1118,7 +1118,7 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
 // S[j * s_stride + s_off + g * RG + r].  Skipped when gate[g] != gate_need.
 // Writes the row partials of tile c: Pr[g][c][i][r].
 // ---------------------------------------------------------------------------
-constexpr int kStageUnroll = 8;    // staging: loads in flight per thread
+constexpr int kStageUnroll = 16;   // staging: loads in flight per thread (8: 0.4 % slower per draw)
 
 template <typename T, int RG>
 __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
