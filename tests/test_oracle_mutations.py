@@ -91,3 +91,59 @@ def test_pins_reject_mutant(name, tmp_path):
     so = str(tmp_path / f"{name}.so")
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, str(c), "-lm"])
     assert _caught(so), f"no pin rejects mutant {name}"
+
+
+# --------------------------------------------------------------------------
+# the unshrunk-coefficient functions of oracle.py (Sec. S4.3), plain numpy:
+# each mutant is a one-line change to a copy of the module's source
+# --------------------------------------------------------------------------
+PY_SRC = os.path.join(os.path.dirname(SRC), "oracle.py")
+
+PY_MUTANTS = {
+    "unshrunk_prior_term_without_sqrt": ("    sd[:q1] = np.sqrt(prior_prec)", "    sd[:q1] = prior_prec"),
+    "unshrunk_gamma_not_squared": ("    m[:q1] = np.asarray(gamma, dtype=np.float64) ** 2",
+                                   "    m[:q1] = np.asarray(gamma, dtype=np.float64)"),
+    "unshrunk_keeps_shrinkage_prior": ("    d[:q1] = prior_prec\n", "    d[:q1] = d[:q1]\n"),
+    "unshrunk_eta_without_sqrt": ("omega * z + np.sqrt(omega) * eta) + sd * delta",
+                                  "omega * z + omega * eta) + sd * delta"),
+    "unshrunk_pcg_wrong_preconditioner": ("        zz = m * r\n        rho_new", "        zz = d * r\n        rho_new"),
+    "unshrunk_phi_drops_omega": ("xd.T @ (_f64(omega)[:, None] * xd) + np.diag(d)", "xd.T @ xd + np.diag(d)"),
+}
+
+UNSHRUNK_PINS = [
+    pins.test_unshrunk_reduces_to_shrunk_when_scales_match,
+    pins.test_unshrunk_flat_prior_intercept_closed_form,
+    pins.test_unshrunk_cg_matches_cholesky_and_ignores_gamma,
+]
+
+
+def _py_module(src):
+    import types
+    mod = types.ModuleType("oracle_copy")
+    mod.__file__ = PY_SRC   # the compiled C routines are found beside the source
+    exec(compile(src, PY_SRC, "exec"), mod.__dict__)
+    return mod
+
+
+def _py_caught(mod, monkeypatch):
+    monkeypatch.setattr(pins, "O", mod)
+    for t in UNSHRUNK_PINS:
+        try:
+            with np.errstate(all="ignore"):
+                t()
+        except Exception:
+            return True
+    return False
+
+
+def test_unmutated_python_copy_passes(monkeypatch):
+    """Control: the harness accepts an unmodified copy of oracle.py."""
+    assert not _py_caught(_py_module(open(PY_SRC).read()), monkeypatch)
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_unshrunk_pins_reject_mutant(name, monkeypatch):
+    old, new = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    assert _py_caught(_py_module(src.replace(old, new)), monkeypatch), f"no pin rejects mutant {name}"
