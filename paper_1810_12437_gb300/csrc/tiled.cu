@@ -608,10 +608,14 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     pl->n = n;
     pl->p = p;
     pl->nnz = nnz;
-    pl->W_c = (int)std::min<int64_t>(w, p);
-    pl->T_c = (int)((p + pl->W_c - 1) / pl->W_c);
-    pl->W_r = (int)std::min<int64_t>(w, n);
-    pl->T_r = (int)((n + pl->W_r - 1) / pl->W_r);
+    // as few tiles (strips) as fit, then equal widths (a multiple of 8), so that
+    // the last one is not a small remainder whose CTAs idle while the others work
+    auto balanced = [&](int64_t len, int *W, int *T) {
+        *T = (int)((len + std::min(w, len) - 1) / std::min(w, len));
+        *W = (int)(*T == 1 ? len : std::min<int64_t>(w, ((len + *T - 1) / *T + 7) & ~int64_t(7)));
+    };
+    balanced(p, &pl->W_c, &pl->T_c);
+    balanced(n, &pl->W_r, &pl->T_r);
     // launch shapes: per group one wave of CTAs over the tiles (strips)
     const size_t smem_c = (size_t)(pl->W_c + 1) * RG * vsize, smem_r = (size_t)(pl->W_r + 1) * RG * vsize;
     const int occ_c = std::max(1, std::min(2, (int)(kSmemPerSm / (smem_c + 2048))));
