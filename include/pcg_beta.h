@@ -71,12 +71,14 @@ enum {
                                    TwoSum, about 48 significant bits at float32 arithmetic
                                    cost; CG scalars, beta and r in float64 */
     PCG_PREC_FX64 = 4           /* fixed-point products: the vectors are float32 pairs as in
-                                   PCG_PREC_DF32; each tile of the gathered vector is
-                                   scaled by a power of two and rounded to 64-bit integers
-                                   (grid: about 2^-52 of the tile's largest value, with room
-                                   for the longest segment's sum), summed exactly in integer
-                                   arithmetic, and each sum converted back to a float32 pair
-                                   (the tiled products only; elsewhere as PCG_PREC_DF32) */
+                                   PCG_PREC_DF32; each tile of the gathered vector is scaled,
+                                   per right-hand side, by a power of two and rounded to
+                                   64-bit integers (grid: 2^(hb-60) of the tile's largest
+                                   value, where a segment sums fewer than 2^hb values, so no
+                                   sum can overflow; about 2^-51 at n = 5e5, p = 5e4), summed
+                                   exactly in integer arithmetic, and each sum converted back
+                                   to a float32 pair (the tiled products only; elsewhere as
+                                   PCG_PREC_DF32) */
 };
 
 /* Stop rules.  With rho = r.(M^-1 r) = ||tau lambda (.) r||^2 (Sec. S4.2):
