@@ -41,6 +41,9 @@ _lib = None
 STOP_RMS = 0
 STOP_RELATIVE = 1
 OK, MAXITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+SUM_PLAIN, SUM_COMPENSATED, SUM_FLOAT32 = 0, 1, 2
+_SUMS = {"plain": SUM_PLAIN, "compensated": SUM_COMPENSATED, "float32": SUM_FLOAT32}
+_VECS = {"f64": 0, "f32x2": 1, "f32": 2}
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +68,15 @@ def _bind(lib):
     lib.oracle_build_b.argtypes = [I64, I64, P, P, P, P, P, D, P, P, P, P]
     lib.oracle_pcg.argtypes = [I64, I64, P, P, P, P, P, P, D, P, D, I, I, I, P, P, P, P]
     lib.oracle_pcg.restype = I
+    lib.oracle_pcg_ex.argtypes = [I64, I64, P, P, P, P, P, P, D, P, P, P, D, I, I, I, I, I, P, P, P, P]
+    lib.oracle_pcg_ex.restype = I
+    lib.oracle_x_mul_comp.argtypes = [I64, P, P, P, P]
+    lib.oracle_xt_mul_comp.argtypes = [I64, P, P, P, P]
+    lib.oracle_dot_comp.argtypes = [I64, P, P]
+    lib.oracle_dot_comp.restype = D
+    lib.oracle_phi_diag.argtypes = [I64, P, P, P, P, D, P]
+    lib.oracle_lsqr.argtypes = [I64, I64, P, P, P, P, P, P, P, D, P, P, D, I, I, I, P, P, P]
+    lib.oracle_lsqr.restype = I
     lib.oracle_dense_phi.argtypes = [I64, I64, P, P, P, P, D, P]
     lib.oracle_cholesky.argtypes = [I64, P]
     lib.oracle_cholesky.restype = I
@@ -141,12 +153,57 @@ def build_b(X, omega, z, lam, tau, eta, delta):
     return b
 
 
-def pcg(X, omega, lam, tau, b, *, tol=1e-6, stop_rule=STOP_RMS, max_iter=10_000,
-        fixed_iters=0, want_hist=False):
-    """Prior-preconditioned CG from beta_0 = 0 (Algorithm S1 in PCG form).
+def x_mul_comp(X, v):
+    """X v with each row sum accumulated by compensated summation."""
+    lib = _load()
+    v = _f64(v)
+    out = np.empty(X.n)
+    lib.oracle_x_mul_comp(X.n, _p(X.row_ptr), _p(X.col_idx), _p(v), _p(out))
+    return out
 
-    Returns (beta, iters, resid, status[, rho_hist]).  ``fixed_iters > 0``
-    runs exactly that many iterations with no stop test.
+
+def xt_mul_comp(X, w):
+    """X^T w with each column sum accumulated by compensated summation."""
+    lib = _load()
+    w = _f64(w)
+    out = np.empty(X.p)
+    lib.oracle_xt_mul_comp(X.p, _p(X.col_ptr), _p(X.row_idx), _p(w), _p(out))
+    return out
+
+
+def dot_comp(a, b):
+    """a . b with the rounded products summed by compensated summation."""
+    lib = _load()
+    a, b = _f64(a), _f64(b)
+    return float(lib.oracle_dot_comp(a.size, _p(a), _p(b)))
+
+
+def phi_diag(X, omega, lam, tau):
+    """diag(Phi) = X^T omega + tau^-2 lambda^-2 for binary X: the Jacobi
+    preconditioner's M (Sec. 2.4)."""
+    lib = _load()
+    omega, lam = _f64(omega), _f64(lam)
+    out = np.empty(X.p)
+    lib.oracle_phi_diag(X.p, _p(X.col_ptr), _p(X.row_idx), _p(omega), _p(lam), float(tau), _p(out))
+    return out
+
+
+def pcg(X, omega, lam, tau, b, *, tol=1e-6, stop_rule=STOP_RMS, max_iter=10_000,
+        fixed_iters=0, want_hist=False, minv=None, beta0=None, sums="plain", vec="f64"):
+    """Preconditioned CG (Algorithm S1 in PCG form).
+
+    Defaults: the prior preconditioner M^-1 = tau^2 Lambda^2 (Sec. 2.4), beta_0 = 0
+    (Sec. 2.7) and plain left-to-right sums.  ``minv`` gives another diagonal
+    M^-1 (the Jacobi preconditioner: 1 / diag(Phi)); ``beta0`` an initial
+    vector (Sec. S4.1); ``sums="compensated"`` accumulates the products' and
+    the dot products' sums by compensated summation (``"float32"``: the
+    products' sums left to right in float32, the dot products compensated); ``vec`` ("f64",
+    "f32x2": float pairs of about 48 bits, "f32") is the storage format of
+    the products' operands and results (s, omega, u and the product X^T u).  The stop rule tests
+    ||tau lambda (.) r|| (Eq. S2) whatever the preconditioner.
+
+    Returns (beta, iters, resid, status[, hist of the stop quantity]).
+    ``fixed_iters > 0`` runs exactly that many iterations with no stop test.
     """
     lib = _load()
     omega, lam, b = _f64(omega), _f64(lam), _f64(b)
@@ -154,14 +211,44 @@ def pcg(X, omega, lam, tau, b, *, tol=1e-6, stop_rule=STOP_RMS, max_iter=10_000,
     iters = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)
     hist = np.full(max(max_iter, fixed_iters) + 1, np.nan) if want_hist else None
-    st = lib.oracle_pcg(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr), _p(X.row_idx),
-                        _p(omega), _p(lam), float(tau), _p(b), float(tol), int(stop_rule),
-                        int(max_iter), int(fixed_iters), _p(beta), ctypes.byref(iters),
-                        ctypes.byref(resid), _p(hist) if want_hist else None)
+    hp = _p(hist) if want_hist else None
+    if minv is None and beta0 is None and sums == "plain" and vec == "f64":
+        st = lib.oracle_pcg(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr), _p(X.row_idx),
+                            _p(omega), _p(lam), float(tau), _p(b), float(tol), int(stop_rule),
+                            int(max_iter), int(fixed_iters), _p(beta), ctypes.byref(iters),
+                            ctypes.byref(resid), hp)
+    else:
+        mv = _f64(minv) if minv is not None else None
+        b0 = _f64(beta0) if beta0 is not None else None
+        st = lib.oracle_pcg_ex(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr),
+                               _p(X.row_idx), _p(omega), _p(lam), float(tau), _p(b),
+                               _p(mv) if mv is not None else None,
+                               _p(b0) if b0 is not None else None,
+                               float(tol), int(stop_rule), int(max_iter), int(fixed_iters),
+                               _SUMS[sums], _VECS[vec], _p(beta), ctypes.byref(iters),
+                               ctypes.byref(resid), hp)
     out = (beta, iters.value, resid.value, st)
     if want_hist:
         out = out + (hist[: iters.value + 1],)
     return out
+
+
+def draw_beta_lsqr(X, omega, z, lam, tau, eta, delta, *, tol=1e-6, stop_rule=STOP_RMS,
+                   max_iter=10_000, sums="plain"):
+    """The draw of Prop. 2.1 by LSQR on the least-squares form (Sec. S7.1, Eq.
+    S6), right-preconditioned by diag(tau lambda); stop rule Eq. S2 on LSQR's
+    ||A^T r|| = ||tau lambda (.) (b - Phi beta)||.  Returns (beta, iters,
+    resid, status)."""
+    lib = _load()
+    omega, z, lam, eta, delta = map(_f64, (omega, z, lam, eta, delta))
+    beta = np.empty(X.p)
+    iters = ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    st = lib.oracle_lsqr(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(X.col_ptr), _p(X.row_idx),
+                         _p(omega), _p(z), _p(lam), float(tau), _p(eta), _p(delta), float(tol),
+                         int(stop_rule), int(max_iter), _SUMS[sums], _p(beta), ctypes.byref(iters),
+                         ctypes.byref(resid))
+    return beta, iters.value, resid.value, st
 
 
 def dense_phi(X, omega, lam, tau):
@@ -201,13 +288,14 @@ def draw_beta_chol(X, omega, z, lam, tau, eta, delta):
 
 
 def draw_beta_cg(X, omega, z, lam, tau, eta, delta, *, tol=1e-6, stop_rule=STOP_RMS,
-                 max_iter=10_000, fixed_iters=0):
-    """CG sampler of Prop. 2.1: b by Eq. 2.3, then PCG on Eq. 2.4.
+                 max_iter=10_000, fixed_iters=0, **pcg_kw):
+    """CG sampler of Prop. 2.1: b by Eq. 2.3, then PCG on Eq. 2.4 (``pcg_kw``:
+    the preconditioner, initial vector and summation options of ``pcg``).
 
     Returns (beta, iters, resid, status)."""
     b = build_b(X, omega, z, lam, tau, eta, delta)
     return pcg(X, omega, lam, tau, b, tol=tol, stop_rule=stop_rule, max_iter=max_iter,
-               fixed_iters=fixed_iters)
+               fixed_iters=fixed_iters, **pcg_kw)
 
 
 def adjoint_from_g(X, omega, z, lam, tau, eta, delta, beta, g, mode="draw"):
@@ -306,19 +394,38 @@ def draw_beta_chol_unshrunk(X, omega, z, lam, tau, eta, delta, prior_prec):
     return np.linalg.solve(l.T, np.linalg.solve(l, b))
 
 
+def stored(vec, x):
+    """x held in a storage format: "f64" as is, "f32x2" a pair of float32
+    (hi = float32(x), lo = float32(x - hi), value hi + lo), "f32" one float32
+    (the same formats as the C oracle's ORACLE_VEC_*)."""
+    x = _f64(x)
+    if vec == "f32x2":
+        hi = x.astype(np.float32).astype(np.float64)
+        return hi + (x - hi).astype(np.float32).astype(np.float64)
+    if vec == "f32":
+        return x.astype(np.float32).astype(np.float64)
+    return x
+
+
 def pcg_unshrunk(X, omega, lam, tau, b, prior_prec, gamma, *, tol=1e-6, stop_rule=STOP_RMS,
-                 max_iter=10_000):
+                 max_iter=10_000, sums="plain", vec="f64"):
     """PCG from beta_0 = 0 (Algorithm S1 in PCG form) on Phi of Sec. S4.3 with
     M^-1 = diag(gamma^2, tau^2 Lambda^2); stop rule Eq. S2 on rho = r . (M^-1 r).
-    Returns (beta, iters, resid, status)."""
+    ``sums="compensated"`` accumulates the products' row and column sums and
+    the dot products by compensated summation (else the C oracle's plain
+    sums and numpy's dot); ``vec`` holds the products' operands and results
+    in a storage format (``stored``).  Returns (beta, iters, resid, status)."""
     omega, b = _f64(omega), _f64(b)
     d, _, m = prior_terms_unshrunk(lam, tau, prior_prec, gamma)
     p = b.size
+    xm, xtm = (x_mul_comp, xt_mul_comp) if sums == "compensated" else (x_mul, xt_mul)
+    dotf = dot_comp if sums == "compensated" else (lambda a, c: float(a @ c))
+    om_s = stored(vec, omega)
     beta = np.zeros(p)
     r = b.copy()
     zz = m * r
     s = zz.copy()
-    rho = float(r @ zz)
+    rho = dotf(r, zz)
     rho0 = rho
 
     def resid(rh):
@@ -327,15 +434,16 @@ def pcg_unshrunk(X, omega, lam, tau, b, prior_prec, gamma, *, tol=1e-6, stop_rul
     if resid(rho) <= tol:
         return beta, 0, resid(rho), OK
     for k in range(1, max_iter + 1):
-        v = xt_mul(X, omega * x_mul(X, s)) + d * s
-        sigma = float(s @ v)
+        u = stored(vec, stored(vec, xm(X, stored(vec, s))) * om_s)
+        v = stored(vec, xtm(X, u)) + d * s
+        sigma = dotf(s, v)
         if not (sigma > 0.0):
             return beta, k, resid(rho), BREAKDOWN
         alpha = rho / sigma
         beta = beta + alpha * s
         r = r - alpha * v
         zz = m * r
-        rho_new = float(r @ zz)
+        rho_new = dotf(r, zz)
         if resid(rho_new) <= tol:
             return beta, k, resid(rho_new), OK
         s = zz + (rho_new / rho) * s

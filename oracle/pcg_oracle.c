@@ -125,12 +125,174 @@ void oracle_build_b(int64_t n, int64_t p,
         b[j] = b[j] + delta[j] / (tau * lam[j]);
 }
 
+/*
+ * Compensated summation (Neumaier 1974, the Kahan-Babuska scheme): the
+ * running sum `s` and, in `c`, the rounding error of every addition, which is
+ * added back at the end.  Used by the ORACLE_SUM_COMPENSATED mode, whose
+ * sums are the same sums as the plain ones, accumulated more accurately.
+ */
+typedef struct { double s, c; } comp_sum;
+
+static void comp_add(comp_sum *a, double x)
+{
+    const double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double comp_value(const comp_sum *a) { return a->s + a->c; }
+
+/* X v with each row sum accumulated by compensated summation. */
+void oracle_x_mul_comp(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const double *v, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        comp_sum acc = {0.0, 0.0};
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            comp_add(&acc, v[col_idx[k]]);
+        out[i] = comp_value(&acc);
+    }
+}
+
+/* X^T w with each column sum accumulated by compensated summation. */
+void oracle_xt_mul_comp(int64_t p, const int64_t *col_ptr, const int32_t *row_idx,
+                        const double *w, double *out)
+{
+    for (int64_t j = 0; j < p; ++j) {
+        comp_sum acc = {0.0, 0.0};
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
+            comp_add(&acc, w[row_idx[k]]);
+        out[j] = comp_value(&acc);
+    }
+}
+
+/* a . b: the rounded products a_j b_j summed by compensated summation. */
+double oracle_dot_comp(int64_t p, const double *a, const double *b)
+{
+    comp_sum acc = {0.0, 0.0};
+    for (int64_t j = 0; j < p; ++j)
+        comp_add(&acc, a[j] * b[j]);
+    return comp_value(&acc);
+}
+
 static double dot(int64_t p, const double *a, const double *b)
 {
     double acc = 0.0;
     for (int64_t j = 0; j < p; ++j)
         acc += a[j] * b[j];
     return acc;
+}
+
+#define ORACLE_SUM_PLAIN 0        /* every sum accumulated left to right, as written above */
+#define ORACLE_SUM_COMPENSATED 1  /* products' and dot products' sums compensated */
+#define ORACLE_SUM_FLOAT32 2      /* products' sums accumulated left to right in float32,
+                                     dot products compensated in float64 */
+
+static double dot_mode(int sum_mode, int64_t p, const double *a, const double *b)
+{
+    return sum_mode == ORACLE_SUM_PLAIN ? dot(p, a, b) : oracle_dot_comp(p, a, b);
+}
+
+/* X v with each row sum accumulated left to right in float32. */
+void oracle_x_mul_f32(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *v, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float acc = 0.0f;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            acc = acc + (float)v[col_idx[k]];
+        out[i] = (double)acc;
+    }
+}
+
+/* X^T w with each column sum accumulated left to right in float32. */
+void oracle_xt_mul_f32(int64_t p, const int64_t *col_ptr, const int32_t *row_idx,
+                       const double *w, double *out)
+{
+    for (int64_t j = 0; j < p; ++j) {
+        float acc = 0.0f;
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
+            acc = acc + (float)w[row_idx[k]];
+        out[j] = (double)acc;
+    }
+}
+
+/* Storage formats of the products' operands (ORACLE_VEC_*): float64 as is,
+ * a pair of float32 (hi = float32(x), lo = float32(x - hi), value hi + lo,
+ * about 48 significant bits), or one float32. */
+#define ORACLE_VEC_F64 0
+#define ORACLE_VEC_F32X2 1
+#define ORACLE_VEC_F32 2
+
+static double stored(int vec, double x)
+{
+    if (vec == ORACLE_VEC_F32X2) {
+        const float hi = (float)x;
+        const float lo = (float)(x - (double)hi);
+        return (double)hi + (double)lo;
+    }
+    if (vec == ORACLE_VEC_F32)
+        return (double)(float)x;
+    return x;
+}
+
+/*
+ * Phi v as oracle_phi_mul, with the products' sums in the given mode and
+ * their operands and results held in the given storage format:
+ *   u = stored(stored(omega) * stored(X stored(v)));  out = stored(X^T u) + d v
+ * (the diagonal term and the output in float64).  work: n doubles.
+ */
+static void phi_mul_mode(int sum_mode, int vec, int64_t n, int64_t p,
+                         const int64_t *row_ptr, const int32_t *col_idx,
+                         const int64_t *col_ptr, const int32_t *row_idx,
+                         const double *omega, const double *lam, double tau,
+                         const double *v, double *out, double *work)
+{
+    if (sum_mode != ORACLE_SUM_COMPENSATED && vec == ORACLE_VEC_F64) {
+        oracle_phi_mul(n, p, row_ptr, col_idx, col_ptr, row_idx, omega, lam, tau, v, out, work);
+        return;
+    }
+    const double *vs = v;
+    double *vr = NULL;
+    if (vec != ORACLE_VEC_F64) {
+        vr = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
+        for (int64_t j = 0; j < p; ++j)
+            vr[j] = stored(vec, v[j]);
+        vs = vr;
+    }
+    if (sum_mode == ORACLE_SUM_COMPENSATED)
+        oracle_x_mul_comp(n, row_ptr, col_idx, vs, work);
+    else if (sum_mode == ORACLE_SUM_FLOAT32)
+        oracle_x_mul_f32(n, row_ptr, col_idx, vs, work);
+    else
+        oracle_x_mul(n, row_ptr, col_idx, vs, work);
+    for (int64_t i = 0; i < n; ++i)
+        work[i] = stored(vec, stored(vec, work[i]) * stored(vec, omega[i]));
+    if (sum_mode == ORACLE_SUM_COMPENSATED)
+        oracle_xt_mul_comp(p, col_ptr, row_idx, work, out);
+    else if (sum_mode == ORACLE_SUM_FLOAT32)
+        oracle_xt_mul_f32(p, col_ptr, row_idx, work, out);
+    else
+        oracle_xt_mul(p, col_ptr, row_idx, work, out);
+    for (int64_t j = 0; j < p; ++j)
+        out[j] = stored(vec, out[j]) + v[j] * prior_prec(tau, lam[j]);
+    free(vr);
+}
+
+/*
+ * Diagonal of Phi, the Jacobi preconditioner M = diag(Phi_11 .. Phi_pp)
+ * (Sec. 2.4): for binary X, Phi_jj = sum over the rows i of column j of
+ * omega_i, plus tau^-2 lambda_j^-2.
+ */
+void oracle_phi_diag(int64_t p, const int64_t *col_ptr, const int32_t *row_idx,
+                     const double *omega, const double *lam, double tau, double *out)
+{
+    oracle_xt_mul(p, col_ptr, row_idx, omega, out);
+    for (int64_t j = 0; j < p; ++j)
+        out[j] = out[j] + prior_prec(tau, lam[j]);
 }
 
 static int stop_met(int rule, double rho, double rho0, int64_t p, double tol)
@@ -147,70 +309,115 @@ static double resid_of(int rule, double rho, double rho0, int64_t p)
     return sqrt(rho / (double)p);
 }
 
+/* ||tau lambda (.) r||^2 = r . (tau^2 lambda^2 r), the squared norm of the
+ * prior-preconditioned residual that Eq. S2 tests. */
+static double stop_norm2(int sum_mode, int64_t p, const double *r, const double *lam, double tau,
+                         double *tmp)
+{
+    for (int64_t j = 0; j < p; ++j)
+        tmp[j] = prior_var(tau, lam[j]) * r[j];
+    return dot_mode(sum_mode, p, r, tmp);
+}
+
 /*
- * Prior-preconditioned CG on Phi beta = b from beta_0 = 0 (Sec. 2.7,
- * Algorithm S1 in PCG form).
+ * Preconditioned CG on Phi beta = b (Algorithm S1 in PCG form), general
+ * form:
+ *   minv   NULL: the prior preconditioner, M^-1 = tau^2 Lambda^2 (Sec. 2.4);
+ *          else the diagonal M^-1 to use (the Jacobi preconditioner of
+ *          Sec. 2.4 passes 1 / diag(Phi)).
+ *   beta0  NULL: beta_0 = 0 (Sec. 2.7); else the initial vector (Sec. S4.1),
+ *          with r_0 = b - Phi beta_0.
+ *   sum_mode  ORACLE_SUM_PLAIN or ORACLE_SUM_COMPENSATED for every sum of
+ *          the products and dot products; ORACLE_SUM_FLOAT32 accumulates the
+ *          products' sums in float32 (left to right) and the dot products
+ *          compensated.
+ *   vec    ORACLE_VEC_F64, or the storage format (ORACLE_VEC_F32X2,
+ *          ORACLE_VEC_F32) in which the products' operands and results are
+ *          held (phi_mul_mode); every other quantity stays float64.
+ * The stop rule always tests the prior-preconditioned residual of Eq. S2,
+ * rho_s = ||tau lambda (.) r||^2: sqrt(rho_s / p) <= tol (RMS), or
+ * sqrt(rho_s / rho_b) <= tol (RELATIVE, rho_b = ||tau lambda (.) b||^2, the
+ * value at beta = 0, so a warm start does not move the target).  With the
+ * prior preconditioner rho_s is the CG's own rho = r.z.
  *
- *   beta = 0; r = b; z = m r; s = z; rho = r.z        (m = tau^2 lambda^2)
+ *   r = b - Phi beta0; z = M^-1 r; s = z; rho = r.z
  *   repeat: v = Phi s; alpha = rho / (s.v)
- *           beta += alpha s; r -= alpha v; z = m r; rho' = r.z; k += 1
- *           stop on rho' (Eq. S2) or k == max_iter
+ *           beta += alpha s; r -= alpha v; z = M^-1 r; rho' = r.z; k += 1
+ *           stop on rho_s (Eq. S2) or k == max_iter
  *           s = z + (rho'/rho) s; rho = rho'
  *
  * fixed_iters > 0 runs exactly that many iterations without testing the
  * stop rule (for same-k comparisons); fixed_iters == 0 uses tol/max_iter.
- * rho_hist (optional, max(max_iter, fixed_iters) + 1 doubles) receives rho
+ * rho_hist (optional, max(max_iter, fixed_iters) + 1 doubles) receives rho_s
  * before the first product and after each product.
- * Returns ORACLE_OK, ORACLE_MAXITER, ORACLE_BREAKDOWN or ORACLE_NONFINITE.
+ * Returns ORACLE_OK, ORACLE_MAXITER, ORACLE_BREAKDOWN (s.v <= 0 or rho <= 0)
+ * or ORACLE_NONFINITE (a NaN or infinite CG scalar).
  */
-int oracle_pcg(int64_t n, int64_t p,
-               const int64_t *row_ptr, const int32_t *col_idx,
-               const int64_t *col_ptr, const int32_t *row_idx,
-               const double *omega, const double *lam, double tau,
-               const double *b, double tol, int stop_rule, int max_iter, int fixed_iters,
-               double *beta, int *iters, double *resid, double *rho_hist)
+int oracle_pcg_ex(int64_t n, int64_t p,
+                  const int64_t *row_ptr, const int32_t *col_idx,
+                  const int64_t *col_ptr, const int32_t *row_idx,
+                  const double *omega, const double *lam, double tau,
+                  const double *b, const double *minv, const double *beta0,
+                  double tol, int stop_rule, int max_iter, int fixed_iters, int sum_mode,
+                  int vec, double *beta, int *iters, double *resid, double *rho_hist)
 {
-    double *r = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
-    double *z = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
-    double *s = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
-    double *v = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
+    const size_t np = (size_t)(p > 0 ? p : 1);
+    double *r = (double *)malloc(sizeof(double) * np);
+    double *z = (double *)malloc(sizeof(double) * np);
+    double *s = (double *)malloc(sizeof(double) * np);
+    double *v = (double *)malloc(sizeof(double) * np);
+    double *tmp = (double *)malloc(sizeof(double) * np);
     double *work = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     int status = ORACLE_OK;
     int k = 0;
 
+    if (beta0) {
+        phi_mul_mode(sum_mode, ORACLE_VEC_F64, n, p, row_ptr, col_idx, col_ptr, row_idx, omega,
+                     lam, tau, beta0, v, work);
+        for (int64_t j = 0; j < p; ++j) {
+            beta[j] = beta0[j];
+            r[j] = b[j] - v[j];            /* r_0 = b - Phi beta_0 */
+        }
+    } else {
+        for (int64_t j = 0; j < p; ++j) {
+            beta[j] = 0.0;
+            r[j] = b[j];                   /* r_0 = b - Phi beta_0 = b */
+        }
+    }
     for (int64_t j = 0; j < p; ++j) {
-        beta[j] = 0.0;
-        r[j] = b[j];                       /* r_0 = b - Phi beta_0 = b */
-        z[j] = prior_var(tau, lam[j]) * r[j];
+        z[j] = minv ? minv[j] * r[j] : prior_var(tau, lam[j]) * r[j];
         s[j] = z[j];
     }
-    double rho = dot(p, r, z);
-    const double rho0 = rho;
-    double rho_new = rho;
-    if (rho_hist) rho_hist[0] = rho;
+    double rho = dot_mode(sum_mode, p, r, z);
+    /* the stop quantity: rho itself under the prior preconditioner */
+    double rho_s = (minv == NULL) ? rho : stop_norm2(sum_mode, p, r, lam, tau, tmp);
+    const double rho_b = (beta0 == NULL) ? rho_s : stop_norm2(sum_mode, p, b, lam, tau, tmp);
+    if (rho_hist) rho_hist[0] = rho_s;
 
-    if (!isfinite(rho)) {
+    if (!isfinite(rho) || !isfinite(rho_s)) {
         status = ORACLE_NONFINITE;
-    } else if (fixed_iters > 0 || !stop_met(stop_rule, rho, rho0, p, tol)) {
+    } else if (fixed_iters > 0 || !stop_met(stop_rule, rho_s, rho_b, p, tol)) {
         int limit = fixed_iters > 0 ? fixed_iters : max_iter;
         if (limit <= 0) status = ORACLE_MAXITER;
         while (k < limit) {
-            oracle_phi_mul(n, p, row_ptr, col_idx, col_ptr, row_idx, omega, lam, tau, s, v, work);
-            double sigma = dot(p, s, v);
+            phi_mul_mode(sum_mode, vec, n, p, row_ptr, col_idx, col_ptr, row_idx, omega, lam, tau,
+                         s, v, work);
+            double sigma = dot_mode(sum_mode, p, s, v);
             if (!isfinite(sigma)) { status = ORACLE_NONFINITE; break; }
             if (sigma <= 0.0 || rho <= 0.0) { status = ORACLE_BREAKDOWN; break; }
             double alpha = rho / sigma;
             for (int64_t j = 0; j < p; ++j) {
                 beta[j] = beta[j] + alpha * s[j];
                 r[j] = r[j] - alpha * v[j];
-                z[j] = prior_var(tau, lam[j]) * r[j];
+                z[j] = minv ? minv[j] * r[j] : prior_var(tau, lam[j]) * r[j];
             }
-            rho_new = dot(p, r, z);
+            double rho_new = dot_mode(sum_mode, p, r, z);
+            rho_s = (minv == NULL) ? rho_new : stop_norm2(sum_mode, p, r, lam, tau, tmp);
             k += 1;
-            if (rho_hist) rho_hist[k] = rho_new;
-            if (!isfinite(rho_new)) { status = ORACLE_NONFINITE; break; }
+            if (rho_hist) rho_hist[k] = rho_s;
+            if (!isfinite(rho_new) || !isfinite(rho_s)) { status = ORACLE_NONFINITE; break; }
             if (fixed_iters == 0) {
-                if (stop_met(stop_rule, rho_new, rho0, p, tol)) break;
+                if (stop_met(stop_rule, rho_s, rho_b, p, tol)) break;
                 if (k == max_iter) { status = ORACLE_MAXITER; break; }
             }
             double gamma = rho_new / rho;
@@ -220,8 +427,164 @@ int oracle_pcg(int64_t n, int64_t p,
         }
     }
     *iters = k;
-    *resid = resid_of(stop_rule, rho_new, rho0, p);
-    free(r); free(z); free(s); free(v); free(work);
+    *resid = resid_of(stop_rule, rho_s, rho_b, p);
+    free(r); free(z); free(s); free(v); free(tmp); free(work);
+    return status;
+}
+
+/*
+ * Prior-preconditioned CG from beta_0 = 0 with plain sums: oracle_pcg_ex
+ * with minv = NULL, beta0 = NULL and ORACLE_SUM_PLAIN.
+ */
+int oracle_pcg(int64_t n, int64_t p,
+               const int64_t *row_ptr, const int32_t *col_idx,
+               const int64_t *col_ptr, const int32_t *row_idx,
+               const double *omega, const double *lam, double tau,
+               const double *b, double tol, int stop_rule, int max_iter, int fixed_iters,
+               double *beta, int *iters, double *resid, double *rho_hist)
+{
+    return oracle_pcg_ex(n, p, row_ptr, col_idx, col_ptr, row_idx, omega, lam, tau, b, NULL, NULL,
+                         tol, stop_rule, max_iter, fixed_iters, ORACLE_SUM_PLAIN, ORACLE_VEC_F64,
+                         beta, iters, resid, rho_hist);
+}
+
+/* X v and X^T w with the sums of a summation mode (plain or compensated). */
+static void x_mode(int sum_mode, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                   const double *v, double *out)
+{
+    if (sum_mode == ORACLE_SUM_COMPENSATED) oracle_x_mul_comp(n, row_ptr, col_idx, v, out);
+    else oracle_x_mul(n, row_ptr, col_idx, v, out);
+}
+
+static void xt_mode(int sum_mode, int64_t p, const int64_t *col_ptr, const int32_t *row_idx,
+                    const double *w, double *out)
+{
+    if (sum_mode == ORACLE_SUM_COMPENSATED) oracle_xt_mul_comp(p, col_ptr, row_idx, w, out);
+    else oracle_xt_mul(p, col_ptr, row_idx, w, out);
+}
+
+/*
+ * LSQR (Paige and Saunders 1982) on the least-squares form of Eq. 2.4 (Sec.
+ * S7.1, Eq. S6): Phi = Xt^T Xt with Xt = [Omega^1/2 X; tau^-1 Lambda^-1] and
+ * Phi beta = Xt^T bt for bt = [Omega^1/2 z + eta; delta], so beta minimises
+ * ||Xt beta - bt||.  LSQR runs on A = Xt D with D = diag(tau lambda) (the
+ * prior preconditioner applied on the right, Sec. 2.4), A = [Omega^1/2 X D; I],
+ * for x = D^-1 beta:
+ *
+ *   beta_1 u_1 = bt;  alpha_1 v_1 = A^T u_1;  w = v_1;  x = 0;
+ *   phibar = beta_1;  rhobar = alpha_1
+ *   repeat (k = 1, 2, ...):
+ *     beta_{k+1} u_{k+1} = A v_k - alpha_k u_k
+ *     alpha_{k+1} v_{k+1} = A^T u_{k+1} - beta_{k+1} v_k
+ *     rho = sqrt(rhobar^2 + beta_{k+1}^2); c = rhobar / rho; s = beta_{k+1} / rho
+ *     theta = s alpha_{k+1}; rhobar = -c alpha_{k+1}; phi = c phibar; phibar = s phibar
+ *     x += (phi / rho) w;  w = v_{k+1} - (theta / rho) w
+ *     stop on ||A^T r_k|| = phibar alpha_{k+1} |c|
+ *
+ * A^T (bt - A x) = D (b - Phi beta) = tau lambda (.) r, the prior-
+ * preconditioned residual of Eq. S2, so the stop rules are those of PCG:
+ * sqrt(||A^T r||^2 / p) <= tol (RMS) or ||A^T r|| / ||A^T bt|| <= tol
+ * (RELATIVE; ||A^T bt|| = alpha_1 beta_1 = ||tau lambda (.) b||).  The
+ * iteration count is the number of x updates (one product with A and one
+ * with A^T each).  beta = D x on return.  Returns ORACLE_OK, ORACLE_MAXITER
+ * or ORACLE_NONFINITE (ORACLE_BREAKDOWN when alpha_1 or beta_1 is not
+ * positive while the stop rule is unmet).  sum_mode: ORACLE_SUM_PLAIN or
+ * ORACLE_SUM_COMPENSATED for the products' sums and the norms.
+ */
+int oracle_lsqr(int64_t n, int64_t p,
+                const int64_t *row_ptr, const int32_t *col_idx,
+                const int64_t *col_ptr, const int32_t *row_idx,
+                const double *omega, const double *z, const double *lam, double tau,
+                const double *eta, const double *delta, double tol, int stop_rule, int max_iter,
+                int sum_mode, double *beta, int *iters, double *resid)
+{
+    const size_t nn = (size_t)(n > 0 ? n : 1), np = (size_t)(p > 0 ? p : 1);
+    double *u = (double *)malloc(sizeof(double) * (nn + np));   /* [top n; bottom p] */
+    double *v = (double *)malloc(sizeof(double) * np);
+    double *w = (double *)malloc(sizeof(double) * np);
+    double *x = (double *)malloc(sizeof(double) * np);
+    double *t = (double *)malloc(sizeof(double) * np);
+    double *tn = (double *)malloc(sizeof(double) * nn);
+    double *dsc = (double *)malloc(sizeof(double) * np);          /* D = tau lambda */
+    int status = ORACLE_OK, k = 0;
+    for (int64_t j = 0; j < p; ++j)
+        dsc[j] = tau * lam[j];
+    /* u = bt / ||bt|| */
+    for (int64_t i = 0; i < n; ++i)
+        u[i] = sqrt(omega[i]) * z[i] + eta[i];
+    for (int64_t j = 0; j < p; ++j)
+        u[n + j] = delta[j];
+    double bet = sqrt(dot_mode(sum_mode, n + p, u, u));
+    if (bet > 0.0)
+        for (int64_t i = 0; i < n + p; ++i) u[i] = u[i] / bet;
+    /* v = A^T u / ||A^T u||,  A^T u = D X^T (Omega^1/2 u_top) + u_bot */
+    for (int64_t i = 0; i < n; ++i)
+        tn[i] = sqrt(omega[i]) * u[i];
+    xt_mode(sum_mode, p, col_ptr, row_idx, tn, t);
+    for (int64_t j = 0; j < p; ++j)
+        v[j] = dsc[j] * t[j] + u[n + j];
+    double alf = sqrt(dot_mode(sum_mode, p, v, v));
+    if (alf > 0.0)
+        for (int64_t j = 0; j < p; ++j) v[j] = v[j] / alf;
+    for (int64_t j = 0; j < p; ++j) {
+        w[j] = v[j];
+        x[j] = 0.0;
+    }
+    double phibar = bet, rhobar = alf;
+    const double ref = alf * bet;                 /* ||A^T bt|| = ||tau lambda (.) b|| */
+    double arnorm = ref;
+    double q = stop_rule == ORACLE_STOP_RELATIVE ? (ref > 0.0 ? arnorm / ref : 0.0)
+                                                 : sqrt(arnorm * arnorm / (double)p);
+    if (!isfinite(q) || !isfinite(alf) || !isfinite(bet)) {
+        status = ORACLE_NONFINITE;
+    } else if (q > tol) {
+        if (!(alf > 0.0) || !(bet > 0.0)) status = ORACLE_BREAKDOWN;
+        else if (max_iter <= 0) status = ORACLE_MAXITER;
+        while (status == ORACLE_OK) {
+            /* u = A v - alpha u,  A v = [Omega^1/2 X (D v); v] */
+            for (int64_t j = 0; j < p; ++j)
+                t[j] = dsc[j] * v[j];
+            x_mode(sum_mode, n, row_ptr, col_idx, t, tn);
+            for (int64_t i = 0; i < n; ++i)
+                u[i] = sqrt(omega[i]) * tn[i] - alf * u[i];
+            for (int64_t j = 0; j < p; ++j)
+                u[n + j] = v[j] - alf * u[n + j];
+            bet = sqrt(dot_mode(sum_mode, n + p, u, u));
+            if (bet > 0.0)
+                for (int64_t i = 0; i < n + p; ++i) u[i] = u[i] / bet;
+            /* v = A^T u - beta v */
+            for (int64_t i = 0; i < n; ++i)
+                tn[i] = sqrt(omega[i]) * u[i];
+            xt_mode(sum_mode, p, col_ptr, row_idx, tn, t);
+            for (int64_t j = 0; j < p; ++j)
+                v[j] = dsc[j] * t[j] + u[n + j] - bet * v[j];
+            alf = sqrt(dot_mode(sum_mode, p, v, v));
+            if (alf > 0.0)
+                for (int64_t j = 0; j < p; ++j) v[j] = v[j] / alf;
+            /* plane rotation */
+            const double rho = sqrt(rhobar * rhobar + bet * bet);
+            const double c = rhobar / rho, sn = bet / rho;
+            const double theta = sn * alf;
+            rhobar = -c * alf;
+            const double phi = c * phibar;
+            phibar = sn * phibar;
+            for (int64_t j = 0; j < p; ++j) {
+                x[j] = x[j] + (phi / rho) * w[j];
+                w[j] = v[j] - (theta / rho) * w[j];
+            }
+            k += 1;
+            arnorm = phibar * alf * fabs(c);
+            q = stop_rule == ORACLE_STOP_RELATIVE ? arnorm / ref : sqrt(arnorm * arnorm / (double)p);
+            if (!isfinite(q) || !isfinite(rho)) { status = ORACLE_NONFINITE; break; }
+            if (q <= tol) break;
+            if (k == max_iter) { status = ORACLE_MAXITER; break; }
+        }
+    }
+    for (int64_t j = 0; j < p; ++j)
+        beta[j] = dsc[j] * x[j];
+    *iters = k;
+    *resid = q;
+    free(u); free(v); free(w); free(x); free(t); free(tn); free(dsc);
     return status;
 }
 

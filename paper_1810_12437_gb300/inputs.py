@@ -153,6 +153,45 @@ def design_from_dense(x: np.ndarray) -> Design:
     return design_from_csc(n, p, col_ptr, cols.astype(np.int32))
 
 
+def perturb_ulps(x: np.ndarray, seed: int) -> np.ndarray:
+    """x with every entry multiplied by 1 + k 2^-52, k drawn uniformly from
+    {-1, 0, 1}: the same input up to about one unit in the last place.  Runs
+    on such copies measure how much an iteration count depends on rounding."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(x, dtype=np.float64)
+    return x * (1.0 + rng.integers(-1, 2, size=x.shape) * 2.0 ** -52)
+
+
+def relabel(P: "Problem", seed: int):
+    """The same single-chain problem with its rows and columns relabelled by
+    seeded random permutations: X'[row_perm[i], col_perm[j]] = X[i, j] and the
+    vectors moved with them.  Returns (P', row_perm, col_perm); a draw of P'
+    at coefficient col_perm[j] corresponds to coefficient j of P.  Every sum
+    of the method runs over the same terms in another order."""
+    rng = np.random.default_rng(seed)
+    X = P.X
+    row_perm = rng.permutation(X.n)
+    col_perm = rng.permutation(X.p)
+    cols = np.repeat(np.arange(X.p, dtype=np.int64), np.diff(X.col_ptr))
+    new_r = row_perm[X.row_idx.astype(np.int64)]
+    new_c = col_perm[cols]
+    order = np.lexsort((new_r, new_c))
+    col_ptr = np.zeros(X.p + 1, dtype=np.int64)
+    np.cumsum(np.bincount(new_c, minlength=X.p), out=col_ptr[1:])
+    X2 = design_from_csc(X.n, X.p, col_ptr, new_r[order].astype(np.int32))
+
+    def mv(v, perm):
+        out = np.empty_like(v)
+        out[perm] = v
+        return out
+
+    P2 = Problem(X=X2, omega=mv(P.omega, row_perm), z=mv(P.z, row_perm), lam=mv(P.lam, col_perm),
+                 tau=P.tau, eta=mv(P.eta, row_perm), delta=mv(P.delta, col_perm),
+                 c=None if P.c is None else mv(P.c, col_perm),
+                 y=None if P.y is None else mv(P.y, row_perm))
+    return P2, row_perm, col_perm
+
+
 def _lambda_half_cauchy(rng, size, inflate_frac=0.0):
     lam = np.abs(rng.standard_cauchy(size=size))
     lam = np.maximum(lam, 1e-300)

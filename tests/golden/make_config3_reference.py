@@ -5,10 +5,23 @@ tol 1e-6 on the paper's RMS rule).
 Only ``oracle/`` computes here.  For each chain the file keeps the iteration
 count, the final stop quantity, ||beta||_2 and beta at 64 seeded sampled
 coordinates, plus a fingerprint of the generated design so that a test can
-tell whether its inputs are the ones this file was made from.
+tell whether its inputs are the ones this file was made from.  Three runs of
+the oracle are kept:
 
-Run:  python tests/golden/make_config3_reference.py [--procs 8]
-(about 16 x 6 CPU-minutes of single-threaded oracle work).
+* ``chains``: plain left-to-right sums (the oracle's default arithmetic);
+* ``compensated``: the same draws with every sum of the products and dot
+  products accumulated by compensated summation;
+* ``compensated_ulp``: the compensated draws on omega and lambda perturbed by
+  about one unit in the last place (``inputs.perturb_ulps``, seeds 9100 + 2r
+  and 9101 + 2r for chain r), which measures how far the iteration count of
+  these ill-conditioned systems moves under rounding alone;
+* ``f32x2`` and ``f32x2_ulp``: the same two compensated runs with the
+  products' operands and results held as float pairs (the oracle's
+  ``vec="f32x2"`` storage, about 48 bits): the reference band of the
+  double-float and fixed-point products.
+
+Run:  python tests/golden/make_config3_reference.py [--procs 8] [--part all|plain|compensated|f32x2]
+(plain: about 16 x 6 CPU-minutes; each compensated run about 16 x 10 CPU-minutes).
 """
 import argparse
 import hashlib
@@ -39,22 +52,42 @@ def sample_indices(p):
     return np.sort(np.random.default_rng(12437).choice(p, size=NSAMPLE, replace=False))
 
 
-def run_chain(r):
+_P = None
+
+
+def _problem():
+    global _P
+    if _P is None:
+        from paper_1810_12437_gb300 import inputs
+        _P = inputs.config3()
+    return _P
+
+
+def run_chain(job):
+    r, kind = job
     from oracle import oracle as O
     from paper_1810_12437_gb300 import inputs
-    P = inputs.config3()
+    P = _problem()
+    omega, lam = P.omega[r], P.lam[r]
+    sums = "plain" if kind == "plain" else "compensated"
+    vec = "f32x2" if kind.startswith("f32x2") else "f64"
+    if kind.endswith("_ulp"):
+        omega = inputs.perturb_ulps(omega, 9100 + 2 * r)
+        lam = inputs.perturb_ulps(lam, 9101 + 2 * r)
     t0 = time.time()
-    beta, k, res, st = O.draw_beta_cg(P.X, P.omega[r], P.z[r], P.lam[r], float(P.tau[r]), P.eta[r],
-                                      P.delta[r], tol=1e-6, stop_rule=O.STOP_RMS, max_iter=20_000)
+    beta, k, res, st = O.draw_beta_cg(P.X, omega, P.z[r], lam, float(P.tau[r]), P.eta[r],
+                                      P.delta[r], tol=1e-6, stop_rule=O.STOP_RMS, max_iter=20_000,
+                                      sums=sums, vec=vec)
     idx = sample_indices(P.X.p)
-    return dict(chain=r, iters=int(k), resid=float(res), status=int(st),
-                beta_norm=float(np.linalg.norm(beta)), sample_idx=idx.tolist(),
-                beta_sample=[float(x) for x in beta[idx]], seconds=time.time() - t0)
+    return kind, dict(chain=r, iters=int(k), resid=float(res), status=int(st),
+                      beta_norm=float(np.linalg.norm(beta)), sample_idx=idx.tolist(),
+                      beta_sample=[float(x) for x in beta[idx]], seconds=time.time() - t0)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--procs", type=int, default=8)
+    ap.add_argument("--part", choices=["all", "plain", "compensated", "f32x2"], default="all")
     args = ap.parse_args()
     from paper_1810_12437_gb300 import inputs
     P = inputs.config3()
@@ -62,13 +95,31 @@ def main():
                 design_fingerprint=design_fingerprint(P.X), tol=1e-6, stop_rule="paper_rms",
                 tau=[float(t) for t in P.tau])
     del P
+    if os.path.exists(OUT):
+        old = json.load(open(OUT))
+        if old.get("design_fingerprint") == meta["design_fingerprint"]:
+            for key in ("chains", "compensated", "compensated_ulp", "f32x2", "f32x2_ulp"):
+                if key in old:
+                    meta[key] = old[key]
+    kinds = {"all": ["plain", "compensated", "compensated_ulp", "f32x2", "f32x2_ulp"],
+             "plain": ["plain"], "compensated": ["compensated", "compensated_ulp"],
+             "f32x2": ["f32x2", "f32x2_ulp"]}[args.part]
+    # longest chains first, so that the pool's tail is short
+    order = list(range(16))
+    if "chains" in meta:
+        order = sorted(range(16), key=lambda r: -meta["chains"][r]["iters"])
+    jobs = [(r, kd) for r in order for kd in kinds]
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.procs) as pool:
-        chains = pool.map(run_chain, range(16))
-    meta["chains"] = sorted(chains, key=lambda c: c["chain"])
+        out = pool.map(run_chain, jobs, chunksize=1)
+    for kd in kinds:
+        key = "chains" if kd == "plain" else kd
+        meta[key] = sorted([c for k2, c in out if k2 == kd], key=lambda c: c["chain"])
     with open(OUT, "w") as f:
         json.dump(meta, f, indent=1)
-    print("wrote", OUT, [c["iters"] for c in meta["chains"]])
+    for kd in ("chains", "compensated", "compensated_ulp", "f32x2", "f32x2_ulp"):
+        if kd in meta:
+            print(kd, [c["iters"] for c in meta[kd]])
 
 
 if __name__ == "__main__":

@@ -23,8 +23,8 @@ MUTANTS = {
     "delta_term_squared_scale": ("b[j] = b[j] + delta[j] / (tau * lam[j]);",
                                  "b[j] = b[j] + delta[j] / (tau * tau * lam[j] * lam[j]);"),
     "residual_sign": ("r[j] = r[j] - alpha * v[j];", "r[j] = r[j] + alpha * v[j];"),
-    "wrong_preconditioner": ("z[j] = prior_var(tau, lam[j]) * r[j];\n            }",
-                             "z[j] = prior_prec(tau, lam[j]) * r[j];\n            }"),
+    "wrong_preconditioner": ("z[j] = minv ? minv[j] * r[j] : prior_var(tau, lam[j]) * r[j];\n            }",
+                             "z[j] = minv ? minv[j] * r[j] : prior_prec(tau, lam[j]) * r[j];\n            }"),
     "gamma_inverted": ("double gamma = rho_new / rho;", "double gamma = rho / rho_new;"),
     "omega_index": ("work[i] = omega[i] * work[i];", "work[i] = omega[i / 2] * work[i];"),
     "prior_diag_dropped": ("out[j] = out[j] + prior_prec(tau, lam[j]) * v[j];",
@@ -34,6 +34,16 @@ MUTANTS = {
     "chol_transposed_operand": ("e -= a[i * p + k] * a[j * p + k];", "e -= a[i * p + k] * a[k * p + j];"),
     "rms_divisor": ("return sqrt(rho / (double)p) <= tol;", "return sqrt(rho) <= tol;"),
     "beta_step_uses_v": ("beta[j] = beta[j] + alpha * s[j];", "beta[j] = beta[j] + alpha * v[j];"),
+    "comp_sum_drops_compensation": ("        a->c += (a->s - t) + x;", "        a->c += 0.0;"),
+    "phi_diag_without_prior": ("        out[j] = out[j] + prior_prec(tau, lam[j]);\n}",
+                               "        out[j] = out[j];\n}"),
+    "warm_start_residual_sign": ("r[j] = b[j] - v[j];            /* r_0 = b - Phi beta_0 */",
+                                 "r[j] = b[j] + v[j];            /* r_0 = b - Phi beta_0 */"),
+    "jacobi_stop_uses_cg_rho": ("rho_s = (minv == NULL) ? rho_new : stop_norm2(sum_mode, p, r, lam, tau, tmp);",
+                                "rho_s = rho_new;"),
+    "lsqr_theta_uses_c": ("const double theta = sn * alf;", "const double theta = c * alf;"),
+    "lsqr_bottom_block_dropped": ("u[n + j] = v[j] - alf * u[n + j];", "u[n + j] = - alf * u[n + j];"),
+    "lsqr_eta_dropped": ("u[i] = sqrt(omega[i]) * z[i] + eta[i];", "u[i] = sqrt(omega[i]) * z[i];"),
 }
 
 # the pins that run against each mutant (the slow statistical ones are left out:
@@ -54,6 +64,13 @@ PIN_TESTS = [
     pins.test_rho_is_true_preconditioned_residual,
     pins.test_stop_rule_rms_is_first_crossing,
     pins.test_thm21_error_bound_and_monotone_phi_norm_error,
+    pins.test_compensated_sums_match_correctly_rounded_sums,
+    pins.test_phi_diag_is_diagonal_of_dense_phi,
+    pins.test_jacobi_pcg_reaches_the_cholesky_solution,
+    pins.test_warm_start,
+    pins.test_lsqr_solves_the_normal_equations,
+    pins.test_lsqr_iterates_equal_pcg_iterates,
+    pins.test_lsqr_residual_estimate_is_eq_s2,
 ]
 
 

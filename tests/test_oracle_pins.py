@@ -438,3 +438,232 @@ def test_unshrunk_cg_matches_cholesky_and_ignores_gamma():
                                         stop_rule=O.STOP_RELATIVE)
         assert st == O.OK
         assert rel(beta, ref) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# compensated sums: the same sums, accumulated more accurately
+# --------------------------------------------------------------------------
+
+def test_compensated_sums_match_correctly_rounded_sums():
+    """Neumaier's compensated summation returns the exactly rounded sum
+    (math.fsum) on sums whose plain left-to-right value is wrong by whole
+    units: one row / column holding 1e16, 1, -1e16, 1, ... and random rows of
+    config 1 (within one unit in the last place of the exact sum)."""
+    big = np.array([1e16, 1.0, -1e16, 1.0, 3.0, 1e16, -1e16, 0.5])
+    X = inputs.design_from_dense(np.ones((1, big.size)))
+    want = math.fsum(big)
+    assert O.x_mul(X, big)[0] != want                     # plain sums lose the small terms
+    assert O.x_mul_comp(X, big)[0] == want
+    assert O.xt_mul_comp(inputs.design_from_dense(np.ones((big.size, 1))), big)[0] == want
+    assert O.dot_comp(big, np.ones_like(big)) == want
+    P = inputs.config1()
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(P.X.p) * 10.0 ** rng.uniform(-8, 8, P.X.p)
+    w = rng.standard_normal(P.X.n) * 10.0 ** rng.uniform(-8, 8, P.X.n)
+    x = P.X.dense()
+    exact_r = np.array([math.fsum(v[x[i] > 0]) for i in range(P.X.n)])
+    exact_c = np.array([math.fsum(w[x[:, j] > 0]) for j in range(P.X.p)])
+    assert np.all(np.abs(O.x_mul_comp(P.X, v) - exact_r) <= np.spacing(np.abs(exact_r)))
+    assert np.all(np.abs(O.xt_mul_comp(P.X, w) - exact_c) <= np.spacing(np.abs(exact_c)))
+    prods = v * v[::-1]
+    assert abs(O.dot_comp(v, v[::-1]) - math.fsum(prods)) <= np.spacing(abs(math.fsum(prods)))
+
+
+def test_compensated_cg_is_the_same_algorithm():
+    """The compensated mode changes only rounding: on config 1 (well enough
+    conditioned that iterates do not amplify rounding) it takes the plain
+    mode's iteration count and reaches the same beta, equal to Cholesky's."""
+    P = inputs.config1()
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    plain = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10, stop_rule=O.STOP_RELATIVE)
+    comp = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10, stop_rule=O.STOP_RELATIVE,
+                 sums="compensated")
+    chol = O.draw_beta_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    assert comp[3] == O.OK and comp[1] == plain[1]
+    assert rel(comp[0], plain[0]) < 1e-11 and rel(comp[0], chol) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# status branches (Sec. 2.4: Phi is SPD in exact arithmetic, so a
+# non-positive curvature or a non-finite scalar is a reported failure)
+# --------------------------------------------------------------------------
+
+def _one_row_problem(omega0):
+    """X = one row of ones (p = 6): Phi = omega_0 1 1^T + diag(d), which is
+    indefinite once omega_0 < -min(d) / p."""
+    p = 6
+    X = inputs.design_from_dense(np.ones((1, p)))
+    lam = np.linspace(0.5, 1.5, p)
+    return X, np.array([omega0]), lam, 1.0
+
+
+def test_breakdown_on_indefinite_phi():
+    """omega_0 = -1e6 makes s . Phi s < 0 for the first direction s = M^-1 b
+    with b = 1: the oracle stops before any product is applied to beta."""
+    X, omega, lam, tau = _one_row_problem(-1e6)
+    b = np.ones(X.p)
+    s = (tau * lam) ** 2 * b
+    phi = omega[0] * np.ones((X.p, X.p)) + np.diag(1.0 / (tau * lam) ** 2)
+    assert s @ phi @ s < 0
+    for sums in ("plain", "compensated"):
+        beta, k, _, st = O.pcg(X, omega, lam, tau, b, tol=1e-12, sums=sums)
+        assert st == O.BREAKDOWN and k == 0 and np.all(beta == 0.0)
+    # the same matrix with omega_0 > 0 is SPD: no breakdown, solution by numpy
+    X, omega, lam, tau = _one_row_problem(0.2)
+    beta, k, _, st = O.pcg(X, omega, lam, tau, b, tol=1e-13, stop_rule=O.STOP_RELATIVE)
+    phi = 0.2 * np.ones((X.p, X.p)) + np.diag(1.0 / (tau * lam) ** 2)
+    assert st == O.OK and rel(beta, np.linalg.solve(phi, b)) < 1e-12
+
+
+def test_nonfinite_inputs_reported():
+    """A NaN in delta makes b, and so rho_0, NaN: NONFINITE before the first
+    product.  An infinite omega makes the first curvature s . Phi s infinite:
+    NONFINITE at the first product, beta still beta_0 = 0."""
+    P = small_problem()
+    delta = P.delta.copy()
+    delta[3] = np.nan
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, delta)
+    assert np.isnan(b[3])
+    beta, k, _, st = O.pcg(P.X, P.omega, P.lam, P.tau, b)
+    assert st == O.NONFINITE and k == 0
+    omega = P.omega.copy()
+    omega[int(np.argmax(np.diff(P.X.row_ptr)))] = np.inf
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    for sums in ("plain", "compensated"):
+        beta, k, _, st = O.pcg(P.X, omega, P.lam, P.tau, b, sums=sums)
+        assert st == O.NONFINITE and k == 0 and np.all(beta == 0.0)
+
+
+# --------------------------------------------------------------------------
+# Jacobi preconditioner (Sec. 2.4, Sec. 3) and initial vectors (Sec. S4.1)
+# --------------------------------------------------------------------------
+
+def test_phi_diag_is_diagonal_of_dense_phi():
+    """Sec. 2.4's Jacobi M = diag(Phi_11 .. Phi_pp) equals the formed Phi's diagonal."""
+    for P in (inputs.config1(), small_problem()):
+        assert rel(O.phi_diag(P.X, P.omega, P.lam, P.tau), np.diag(dense_phi_numpy(P))) < 1e-15
+
+
+def test_jacobi_pcg_reaches_the_cholesky_solution():
+    """PCG with M^-1 = 1 / diag(Phi) solves the same system (config 1, relative
+    stop 1e-12 on the prior-preconditioned residual of Eq. S2)."""
+    P = inputs.config1()
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    minv = 1.0 / O.phi_diag(P.X, P.omega, P.lam, P.tau)
+    chol = O.draw_beta_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    beta, k, res, st = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-12,
+                             stop_rule=O.STOP_RELATIVE, minv=minv)
+    assert st == O.OK and 0 < k < P.X.p and res <= 1e-12
+    assert rel(beta, chol) < 1e-9
+    # the reported stop quantity is the prior-preconditioned norm of the true residual
+    rt = P.tau * P.lam * (b - O.phi_mul(P.X, P.omega, P.lam, P.tau, beta))
+    rb = P.tau * P.lam * b
+    assert abs(np.linalg.norm(rt) / np.linalg.norm(rb) - res) <= 1e-3 * res + 1e-15
+
+
+def test_jacobi_is_prior_preconditioner_without_data():
+    """With X = 0, diag(Phi) = tau^-2 lambda^-2 = M: the Jacobi and prior
+    preconditioners coincide, and both solve in one iteration (Thm 2.2, k = 0)."""
+    P = small_problem()
+    X0 = inputs.design_from_dense(np.zeros((P.X.n, P.X.p)))
+    b = O.build_b(X0, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    minv = 1.0 / O.phi_diag(X0, P.omega, P.lam, P.tau)
+    prior = O.pcg(X0, P.omega, P.lam, P.tau, b, tol=1e-14)
+    jac = O.pcg(X0, P.omega, P.lam, P.tau, b, tol=1e-14, minv=minv)
+    assert prior[1] == jac[1] == 1
+    assert rel(jac[0], (P.tau * P.lam) ** 2 * b) < 1e-15 and rel(jac[0], prior[0]) < 1e-15
+
+
+def test_warm_start():
+    """Sec. S4.1: an initial vector beta_0 gives r_0 = b - Phi beta_0.
+    beta_0 = 0 is the default exactly; beta_0 at the solution stops before any
+    product; beta_0 = an early iterate is refined to the Cholesky solution, and
+    its first stop quantity is the norm of b - Phi beta_0."""
+    P = inputs.config1()
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    base = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10, stop_rule=O.STOP_RELATIVE)
+    zero = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10, stop_rule=O.STOP_RELATIVE,
+                 beta0=np.zeros(P.X.p))
+    assert zero[1] == base[1] and np.array_equal(zero[0], base[0])
+    chol = O.draw_beta_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    at = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-8, stop_rule=O.STOP_RELATIVE, beta0=chol)
+    assert at[1] == 0 and at[3] == O.OK and np.array_equal(at[0], chol)
+    early = O.pcg(P.X, P.omega, P.lam, P.tau, b, fixed_iters=4)[0]
+    beta, k, res, st, hist = O.pcg(P.X, P.omega, P.lam, P.tau, b, tol=1e-10,
+                                   stop_rule=O.STOP_RELATIVE, beta0=early, want_hist=True)
+    r0 = P.tau * P.lam * (b - P.X.dense().T @ (P.omega * (P.X.dense() @ early))
+                          - early / (P.tau * P.lam) ** 2)
+    assert abs(hist[0] - r0 @ r0) <= 1e-10 * (r0 @ r0)
+    assert st == O.OK and 0 < k < base[1] + 5 and rel(beta, chol) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# LSQR on the least-squares form (Sec. S7.1, Eq. S6)
+# --------------------------------------------------------------------------
+
+def test_lsqr_solves_the_normal_equations():
+    """Eq. S6: the minimiser of ||Xt beta - bt|| solves Phi beta = b.  On
+    config 1 LSQR reaches the Cholesky draw and takes CG's iteration count
+    (the two are the same Krylov method on this system)."""
+    P = inputs.config1()
+    chol = O.draw_beta_chol(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    beta, k, res, st = O.draw_beta_lsqr(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-10,
+                                        stop_rule=O.STOP_RELATIVE)
+    k_cg = O.draw_beta_cg(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-10,
+                          stop_rule=O.STOP_RELATIVE)[1]
+    assert st == O.OK and res <= 1e-10 and k == k_cg
+    assert rel(beta, chol) < 1e-8
+
+
+def test_lsqr_iterates_equal_pcg_iterates():
+    """LSQR with A = Xt diag(tau lambda) and PCG with M^-1 = tau^2 lambda^2
+    build the same iterates in exact arithmetic: at a fixed k on a
+    well-conditioned instance they agree to rounding (measured 3e-16 at k =
+    1 growing to 5e-10 at k = 9 as the residual shrinks)."""
+    P = small_problem(n=200, p=40, tau=0.3)
+    P.lam = np.random.default_rng(2).uniform(0.5, 2.0, P.X.p)
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    for k, bound in ((1, 1e-14), (2, 1e-13), (5, 1e-11), (9, 5e-9)):
+        ls, kk, _, st = O.draw_beta_lsqr(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=0.0,
+                                         max_iter=k)
+        cg = O.pcg(P.X, P.omega, P.lam, P.tau, b, fixed_iters=k)[0]
+        assert st == O.MAXITER and kk == k and rel(ls, cg) < bound, k
+
+
+def test_lsqr_residual_estimate_is_eq_s2():
+    """LSQR's ||A^T r|| = phibar alpha |c| is the prior-preconditioned
+    residual of Eq. S2, recomputed here from b - Phi beta."""
+    P = inputs.make_problem(4000, 600, -3.0, -1.0, seed=44, tau=1e-2, inflate_frac=0.02)
+    beta, k, res, st = O.draw_beta_lsqr(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-7)
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    rt = P.tau * P.lam * (b - dense_phi_numpy(P) @ beta)
+    assert st == O.OK and k > 5 and res <= 1e-7
+    assert abs(np.sqrt(np.mean(rt ** 2)) - res) <= 1e-3 * res
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_lsqr_low_rank_and_empty_design(k):
+    """Thm 2.2 (n = k rows: at most k + 1 iterations) and X = 0 (one
+    iteration, beta = tau^2 lambda^2 b)."""
+    rng = np.random.default_rng(500 + k)
+    x = (rng.uniform(size=(k, 60)) < 0.3).astype(float)
+    P = inputs.Problem(inputs.design_from_dense(x), rng.uniform(0.05, 0.25, k), rng.standard_normal(k),
+                       rng.uniform(0.5, 2.0, 60), 0.3, rng.standard_normal(k), rng.standard_normal(60))
+    _, kk, _, st = O.draw_beta_lsqr(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-10,
+                                    stop_rule=O.STOP_RELATIVE)
+    assert st == O.OK and kk <= k + 1
+    Q = small_problem()
+    Q.X = inputs.design_from_dense(np.zeros((Q.X.n, Q.X.p)))
+    beta, kk, _, st = O.draw_beta_lsqr(Q.X, Q.omega, Q.z, Q.lam, Q.tau, Q.eta, Q.delta, tol=1e-12)
+    assert st == O.OK and kk == 1 and rel(beta, Q.tau * Q.lam * Q.delta) < 1e-14
+
+
+def test_lsqr_nonfinite_input_reported():
+    """A NaN in delta makes bt, and so beta_1, NaN: NONFINITE under both stop
+    rules, before any x update."""
+    P = small_problem()
+    P.delta = P.delta.copy()
+    P.delta[2] = np.nan
+    for rule in (O.STOP_RMS, O.STOP_RELATIVE):
+        _, k, _, st = O.draw_beta_lsqr(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, stop_rule=rule)
+        assert st == O.NONFINITE and k == 0
