@@ -83,8 +83,18 @@ enum {
 
 /* Stop rules.  With rho = r.(M^-1 r) = ||tau lambda (.) r||^2 (Sec. S4.2):
  *   PCG_STOP_PAPER_RMS  stop when sqrt(rho / p) <= tol          (Eq. S2)
- *   PCG_STOP_RELATIVE   stop when sqrt(rho / rho_0) <= tol      (rho_0 at beta_0 = 0) */
+ *   PCG_STOP_RELATIVE   stop when sqrt(rho / rho_0) <= tol      (rho_0 at beta_0 = 0)
+ * (with the Jacobi preconditioner or a warm start, rho is still ||tau lambda (.) r||^2
+ * and rho_0 = ||tau lambda (.) b||^2). */
 enum { PCG_STOP_PAPER_RMS = 0, PCG_STOP_RELATIVE = 1 };
+
+/* Preconditioners of the single-RHS CG (Sec. 2.4): the prior precision
+ * M = tau^-2 Lambda^-2 (the paper's choice), or the Jacobi preconditioner
+ * M = diag(Phi_11 .. Phi_pp), diag(Phi)_j = sum_{i: X_ij = 1} omega_i + tau^-2
+ * lambda_j^-2 for binary X (the alternative Sec. 2.4 names and Sec. 3 compares).
+ * Whatever the preconditioner, the stop rule tests the prior-preconditioned
+ * residual of Eq. S2, ||tau lambda (.) r||, so both stop at the same accuracy. */
+enum { PCG_PRECOND_PRIOR = 0, PCG_PRECOND_JACOBI = 1 };
 
 /* Adjoint modes: gradient with b as an input, or with b built inside from (z, eta, delta). */
 enum { PCG_ADJ_SOLVE = 0, PCG_ADJ_DRAW = 1 };
@@ -112,6 +122,20 @@ typedef struct pcg_options {
     const char *autotune_cache; /* host path of a text file caching tuned launch shapes, or NULL */
     int profile;                /* 1: time every kernel with CUDA events on the context stream
                                    (forces plain launches); read with pcg_profile_entry */
+    double idle_limit_s;        /* uneven batch: a CTA that finds no work gives up, and the
+                                   call returns PCG_TIMEOUT, once no tile of any problem has
+                                   completed for this many seconds; default 2.0, accepted
+                                   range [1e-6, 3600] (PCG_BADARG at pcg_ctx_create otherwise) */
+    int preconditioner;         /* PCG_PRECOND_*, default PCG_PRECOND_PRIOR; pcg_draw_beta and
+                                   pcg_solve (and the adjoint's solve) only: the batched and
+                                   uneven entry points return PCG_BADARG for JACOBI */
+    int warm_start;             /* 1: pcg_draw_beta and pcg_solve start CG from the initial
+                                   vector beta_0 that the output buffer holds on entry (Sec.
+                                   S4.1; r_0 = b - Phi beta_0, one float64 product), instead
+                                   of beta_0 = 0; the RELATIVE rule still measures against
+                                   ||tau lambda (.) b|| so the target does not move.  Default 0;
+                                   the batched, uneven and adjoint entry points return
+                                   PCG_BADARG when it is set */
 } pcg_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -187,6 +211,24 @@ pcg_status pcg_draw_beta(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_cs
                          double *beta, int *iters, double *resid);
 
 /*
+ * The same draw by LSQR (Paige and Saunders 1982) on the least-squares form
+ * of Sec. S7.1 (Eq. S6): beta minimises ||Xt beta - bt|| with Xt = [Omega^1/2 X;
+ * tau^-1 Lambda^-1] and bt = [Omega^1/2 z + eta; delta], whose normal equations
+ * are Phi beta = b of Eq. 2.3-2.4.  LSQR is run on Xt diag(tau lambda) (the
+ * prior preconditioner applied on the right), so its estimate of ||A^T r||
+ * equals ||tau lambda (.) (b - Phi beta)|| and it stops under the context's
+ * stop rule exactly as pcg_draw_beta does.  In exact arithmetic its iterates
+ * are those of the prior-preconditioned CG.  Arithmetic: float64 products and
+ * scalars whatever the context's precision.  Arguments and outputs as
+ * pcg_draw_beta; PCG_BADARG while unshrunk coefficients, the Jacobi
+ * preconditioner or warm starts are set on the context.
+ */
+pcg_status pcg_draw_beta_lsqr(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
+                              const double *omega, const double *z, const double *lambda, double tau,
+                              const double *eta, const double *delta, double tol, int max_iter,
+                              double *beta, int *iters, double *resid);
+
+/*
  * CG solve of Phi x = rhs (Eq. 2.4) for a given right-hand side (no Eq. 2.3
  * step); same outputs as pcg_draw_beta.  Used by the adjoint, whose second
  * solve Phi g = c shares Phi and the preconditioner.
@@ -251,6 +293,20 @@ pcg_status pcg_adjoint(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
                        const double *grad_beta, int mode, double tol, int max_iter,
                        double *g_b, double *g_omega, double *g_loglambda, double *g_logtau,
                        int *iters, double *resid);
+
+/*
+ * Whether the shared-memory tiled products serve a design of this shape:
+ * returns 1 and the tile counts (host outputs, may be NULL) if they do, 0 if
+ * the calls fall back to the untiled products (empty X, or a shape whose
+ * padded 16-bit index stream or segment count exceeds the plan's 32-bit
+ * positions and int counts).  rhs_group: right-hand sides staged together
+ * (1 for the single-RHS path; 1, 2 or 4 in the batched path); precision:
+ * PCG_PREC_*.  Host arithmetic only (no context, no GPU).  The paper's
+ * products are plain sparse-BLAS calls (Sec. S7.2); this is the layout of
+ * Sec. 1's two products on GB300.
+ */
+int pcg_tiled_plan_applies(int64_t n, int64_t p, int64_t nnz, int precision, int rhs_group,
+                           int *col_tiles, int *row_strips);
 
 /*
  * Measurement hooks (not in the paper; the paper times each linear-algebra

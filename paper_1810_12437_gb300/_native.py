@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN", 3: "NONFINITE", 4: "BADAR
 PREC = {"fp64": 0, "fp32_refined": 1, "fp32": 2, "df32": 3, "fx64": 4}
 STOP = {"rms": 0, "paper_rms": 0, "relative": 1}
 ADJ = {"solve": 0, "draw": 1}
+PRECOND = {"prior": 0, "jacobi": 1}
 
 
 class PcgError(RuntimeError):
@@ -47,7 +48,9 @@ class _Csc(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("reliable_k", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("autotune_cache", ctypes.c_char_p), ("profile", ctypes.c_int)]
+                ("autotune_cache", ctypes.c_char_p), ("profile", ctypes.c_int),
+                ("idle_limit_s", ctypes.c_double), ("preconditioner", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -94,6 +97,8 @@ def load_library(path: str = LIB_PATH):
             "pcg_profile_reset": ([P], None),
             "pcg_last_kernel_launches": ([P], I64),
             "pcg_phi_mul_noalloc": ([pCsr, pCsc, P, P, D, P, P, P], I),
+            "pcg_tiled_plan_applies": ([I64, I64, I64, I, I, pI, pI], I),
+            "pcg_draw_beta_lsqr": ([P, pCsr, pCsc, P, P, P, D, P, P, D, I, P, pI, pD], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -108,7 +113,7 @@ def exported_symbols() -> Sequence[str]:
             "pcg_check_design", "pcg_build_rhs", "pcg_phi_mul", "pcg_draw_beta", "pcg_solve",
             "pcg_draw_beta_batched", "pcg_draw_beta_uneven", "pcg_adjoint", "pcg_profile_count",
             "pcg_profile_entry", "pcg_profile_reset", "pcg_last_kernel_launches",
-            "pcg_phi_mul_noalloc", "pcg_set_unshrunk"]
+            "pcg_phi_mul_noalloc", "pcg_set_unshrunk", "pcg_tiled_plan_applies", "pcg_draw_beta_lsqr"]
 
 
 # ---------------------------------------------------------------------------
@@ -179,7 +184,8 @@ class Context:
 
     def __init__(self, precision="df32", reliable_k=50, stop_rule="rms", use_graph=True,
                  stream: Optional[torch.cuda.Stream] = None, autotune_cache: Optional[str] = None,
-                 profile: bool = False):
+                 profile: bool = False, idle_limit_s: Optional[float] = None,
+                 preconditioner: str = "prior", warm_start: bool = False):
         lib = load_library()
         opt = _Options()
         lib.pcg_options_default(ctypes.byref(opt))
@@ -190,6 +196,11 @@ class Context:
         self._cache_path = autotune_cache.encode() if autotune_cache else None
         opt.autotune_cache = self._cache_path
         opt.profile = 1 if profile else 0
+        if idle_limit_s is not None:
+            opt.idle_limit_s = float(idle_limit_s)
+        opt.preconditioner = PRECOND[preconditioner] if isinstance(preconditioner, str) else int(preconditioner)
+        opt.warm_start = 1 if warm_start else 0
+        self.warm_start = bool(warm_start)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         self.precision = precision
@@ -300,14 +311,26 @@ class DrawResult:
     status: object
 
 
+def _warm_out(ctx, out, p, dev):
+    """The output buffer; with the context's warm start it must be given and
+    hold beta_0 (Sec. S4.1)."""
+    f = torch.float64
+    if out is None:
+        if getattr(ctx, "warm_start", False):
+            raise ValueError("warm_start: pass out= holding the initial vector beta_0")
+        return torch.empty(p, dtype=f, device=dev)
+    return _dev(out, f, p, "out", dev)
+
+
 def pcg_draw_beta(ctx, X, omega, z, lam, tau, eta, delta, tol=1e-6, max_iter=10_000, out=None):
-    """One draw of beta ~ N(Phi^-1 X^T Omega z, Phi^-1) (Prop. 2.1)."""
+    """One draw of beta ~ N(Phi^-1 X^T Omega z, Phi^-1) (Prop. 2.1).  With a
+    warm-start context, `out` holds beta_0 on entry and the draw on return."""
     f = torch.float64
     dev = X.device
     for name, t, m in (("omega", omega, X.n), ("z", z, X.n), ("eta", eta, X.n),
                        ("lambda", lam, X.p), ("delta", delta, X.p)):
         _dev(t, f, m, name, dev)
-    out = torch.empty(X.p, dtype=f, device=dev) if out is None else _dev(out, f, X.p, "out", dev)
+    out = _warm_out(ctx, out, X.p, dev)
     csr, csc = X.csr(), X.csc()
     it, rs = ctypes.c_int(0), ctypes.c_double(0.0)
     with torch.cuda.device(ctx.device):
@@ -318,14 +341,34 @@ def pcg_draw_beta(ctx, X, omega, z, lam, tau, eta, delta, tol=1e-6, max_iter=10_
     return DrawResult(out, it.value, rs.value, st)
 
 
+def pcg_draw_beta_lsqr(ctx, X, omega, z, lam, tau, eta, delta, tol=1e-6, max_iter=10_000, out=None):
+    """The draw of Prop. 2.1 by LSQR on the least-squares form (Sec. S7.1),
+    float64, under the context's stop rule."""
+    f = torch.float64
+    dev = X.device
+    for name, t, m in (("omega", omega, X.n), ("z", z, X.n), ("eta", eta, X.n),
+                       ("lambda", lam, X.p), ("delta", delta, X.p)):
+        _dev(t, f, m, name, dev)
+    out = torch.empty(X.p, dtype=f, device=dev) if out is None else _dev(out, f, X.p, "out", dev)
+    csr, csc = X.csr(), X.csc()
+    it, rs = ctypes.c_int(0), ctypes.c_double(0.0)
+    with torch.cuda.device(ctx.device):
+        st = ctx.check(ctx._lib.pcg_draw_beta_lsqr(ctx.handle, ctypes.byref(csr), ctypes.byref(csc),
+                                                   _ptr(omega), _ptr(z), _ptr(lam), float(tau), _ptr(eta),
+                                                   _ptr(delta), float(tol), int(max_iter), _ptr(out),
+                                                   ctypes.byref(it), ctypes.byref(rs)))
+    return DrawResult(out, it.value, rs.value, st)
+
+
 def pcg_solve(ctx, X, omega, lam, tau, rhs, tol=1e-6, max_iter=10_000, out=None):
-    """Solve Phi x = rhs by the same prior-preconditioned CG."""
+    """Solve Phi x = rhs by the same preconditioned CG (warm start as in
+    pcg_draw_beta)."""
     f = torch.float64
     dev = X.device
     _dev(omega, f, X.n, "omega", dev)
     _dev(lam, f, X.p, "lambda", dev)
     _dev(rhs, f, X.p, "rhs", dev)
-    out = torch.empty(X.p, dtype=f, device=dev) if out is None else _dev(out, f, X.p, "out", dev)
+    out = _warm_out(ctx, out, X.p, dev)
     csr, csc = X.csr(), X.csc()
     it, rs = ctypes.c_int(0), ctypes.c_double(0.0)
     with torch.cuda.device(ctx.device):
@@ -445,6 +488,18 @@ def profile_table(ctx: Context) -> dict:
 
 
 NOALLOC_MAX_N = 1048576
+
+
+def pcg_tiled_plan_applies(n, p, nnz, precision="df32", rhs_group=1):
+    """(column tiles, row strips) of the shared-memory tiled products for a
+    design of this shape, or None when the calls use the untiled products.
+    Host arithmetic only."""
+    lib = load_library()
+    tc, tr = ctypes.c_int(0), ctypes.c_int(0)
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    ok = lib.pcg_tiled_plan_applies(int(n), int(p), int(nnz), prec, int(rhs_group), ctypes.byref(tc),
+                                    ctypes.byref(tr))
+    return (tc.value, tr.value) if ok else None
 
 
 def pcg_phi_mul_noalloc(X, omega, lam, tau, v, out, stream=None):

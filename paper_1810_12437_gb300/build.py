@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_pcg_beta.so")
-SOURCES = ["capi.cu", "single.cu", "batched.cu", "uneven.cu", "adjoint.cu", "noalloc.cu", "tiled.cu"]
+SOURCES = ["capi.cu", "single.cu", "batched.cu", "uneven.cu", "adjoint.cu", "noalloc.cu", "tiled.cu",
+           "lsqr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-diag-suppress", "177", f"-I{os.path.join(ROOT, 'include')}"]

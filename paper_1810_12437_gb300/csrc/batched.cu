@@ -1280,17 +1280,18 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
             PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ws.desc, hd, sizeof(BatchDesc), cudaMemcpyHostToDevice, ctx->stream));
             float ms = 0.f;
             for (int rep = 0; rep < 2; ++rep) {   // the first run builds the graph
-                cudaEvent_t e0, e1;
-                cudaEventCreate(&e0);
-                cudaEventCreate(&e1);
-                cudaEventRecord(e0, ctx->stream);
-                st = batched_once(ctx, ws, RP, refined, nrhs, 12, bp, hsc, hflags);
-                cudaEventRecord(e1, ctx->stream);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                cudaError_t ce = cudaEventCreate(&e0);
+                if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, ctx->stream);
+                if (ce == cudaSuccess) st = batched_once(ctx, ws, RP, refined, nrhs, 12, bp, hsc, hflags);
+                if (ce == cudaSuccess && st == PCG_OK) ce = cudaEventRecord(e1, ctx->stream);
+                if (ce == cudaSuccess && st == PCG_OK) ce = cudaEventSynchronize(e1);
+                if (ce == cudaSuccess && st == PCG_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
                 if (st != PCG_OK) return st;
+                if (ce != cudaSuccess) return cuda_error(ctx, ce, "timing an autotune candidate");
             }
             if (ms < best) {
                 best = ms;

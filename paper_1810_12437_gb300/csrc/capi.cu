@@ -12,6 +12,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "tiled.h"
 
 namespace pcg {
 
@@ -219,6 +220,17 @@ __global__ void k_unshrunk(const double *__restrict__ prec, const double *__rest
 
 extern "C" {
 
+int pcg_tiled_plan_applies(int64_t n, int64_t p, int64_t nnz, int precision, int rhs_group,
+                           int *col_tiles, int *row_strips) {
+    if (precision < 0 || precision > PCG_PREC_FX64 || rhs_group <= 0) return 0;
+    const int vsize = pcg::tiled_vtype(precision) == pcg::kVtF32 ? 4 : 8;
+    int Wc = 0, Tc = 0, Wr = 0, Tr = 0;
+    if (!pcg::tiled_geometry(n, p, nnz, rhs_group, vsize, &Wc, &Tc, &Wr, &Tr)) return 0;
+    if (col_tiles) *col_tiles = Tc;
+    if (row_strips) *row_strips = Tr;
+    return 1;
+}
+
 pcg_status pcg_options_default(pcg_options *opt) {
     if (!opt) return PCG_BADARG;
     opt->precision = PCG_PREC_DF32;
@@ -227,6 +239,9 @@ pcg_status pcg_options_default(pcg_options *opt) {
     opt->use_graph = 1;
     opt->autotune_cache = nullptr;
     opt->profile = 0;
+    opt->idle_limit_s = 2.0;
+    opt->preconditioner = PCG_PRECOND_PRIOR;
+    opt->warm_start = 0;
     return PCG_OK;
 }
 
@@ -237,7 +252,10 @@ pcg_status pcg_ctx_create(pcg_ctx **out, const pcg_options *opt, void *stream) {
     if (opt) ctx->opt = *opt;
     else pcg_options_default(&ctx->opt);
     if (ctx->opt.precision < 0 || ctx->opt.precision > PCG_PREC_FX64 || ctx->opt.stop_rule < 0 ||
-        ctx->opt.stop_rule > 1 || ctx->opt.reliable_k < 0) {
+        ctx->opt.stop_rule > 1 || ctx->opt.reliable_k < 0 ||
+        !(ctx->opt.idle_limit_s >= 1e-6 && ctx->opt.idle_limit_s <= 3600.0) ||
+        (ctx->opt.preconditioner != PCG_PRECOND_PRIOR && ctx->opt.preconditioner != PCG_PRECOND_JACOBI) ||
+        (ctx->opt.warm_start != 0 && ctx->opt.warm_start != 1)) {
         delete ctx;
         return PCG_BADARG;
     }
@@ -387,6 +405,7 @@ static pcg_status draw_or_solve(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *
     d.tol = tol;
     d.max_iter = max_iter;
     d.stop_rule = ctx->opt.stop_rule;
+    d.warm = ctx->opt.warm_start;
     return run_single(ctx, d, ctx->opt.precision, rhs ? 1 : 0, iters, resid);
 }
 
@@ -396,6 +415,27 @@ pcg_status pcg_draw_beta(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, con
                          double *resid) {
     return draw_or_solve(ctx, Xr, Xc, omega, z, lambda, tau, eta, delta, nullptr, tol, max_iter,
                          beta, iters, resid);
+}
+
+pcg_status pcg_draw_beta_lsqr(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *omega,
+                              const double *z, const double *lambda, double tau, const double *eta,
+                              const double *delta, double tol, int max_iter, double *beta, int *iters,
+                              double *resid) {
+    if (!ctx) return PCG_BADARG;
+    ctx->last_launches = 0;
+    if (!iters || !resid) return set_error(ctx, PCG_BADARG, "NULL host output");
+    *iters = 0;
+    *resid = 0.0;
+    pcg_status st = check_shapes(ctx, Xr, Xc);
+    if (st != PCG_OK) return st;
+    if (bad_scalar(tau)) return set_error(ctx, PCG_BADARG, "tau must be positive and finite");
+    if (!(tol >= 0.0) || max_iter < 0) return set_error(ctx, PCG_BADARG, "tol >= 0 and max_iter >= 0 required");
+    if (ctx->unshrunk_q1 > 0 || ctx->opt.preconditioner != PCG_PRECOND_PRIOR || ctx->opt.warm_start)
+        return set_error(ctx, PCG_BADARG, "LSQR runs the shrinkage model's prior preconditioner from 0");
+    if (Xr->p == 0) return PCG_OK;
+    if ((Xr->n > 0 && (!omega || !z || !eta)) || !lambda || !delta || !beta)
+        return set_error(ctx, PCG_BADARG, "NULL vector");
+    return run_lsqr(ctx, Xr, Xc, omega, z, lambda, tau, eta, delta, tol, max_iter, beta, iters, resid);
 }
 
 pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *omega,
@@ -416,6 +456,8 @@ pcg_status pcg_draw_beta_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc 
     pcg_status st = check_shapes(ctx, Xr, Xc);
     if (st != PCG_OK) return st;
     if (nrhs < 1 || nrhs > kMaxBatch) return set_error(ctx, PCG_BADARG, "nrhs must be in [1, 32]");
+    if (ctx->opt.preconditioner != PCG_PRECOND_PRIOR || ctx->opt.warm_start)
+        return set_error(ctx, PCG_BADARG, "the batched path runs the prior preconditioner from beta_0 = 0");
     if (!iters || !resid || !status) return set_error(ctx, PCG_BADARG, "NULL host output");
     if (!(tol >= 0.0) || max_iter < 0) return set_error(ctx, PCG_BADARG, "tol >= 0 and max_iter >= 0 required");
     for (int r = 0; r < nrhs; ++r) {
@@ -439,6 +481,8 @@ pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *prob
     if (!(tol >= 0.0) || max_iter < 0) return set_error(ctx, PCG_BADARG, "tol >= 0 and max_iter >= 0 required");
     if (ctx->unshrunk_q1 > 0)
         return set_error(ctx, PCG_BADARG, "the uneven batch takes no unshrunk coefficients (pcg_set_unshrunk)");
+    if (ctx->opt.preconditioner != PCG_PRECOND_PRIOR || ctx->opt.warm_start)
+        return set_error(ctx, PCG_BADARG, "the uneven batch runs the prior preconditioner from beta_0 = 0");
     for (int q = 0; q < nprob; ++q) {
         pcg_status st = check_shapes(ctx, &probs[q].X_csr, &probs[q].X_csc);
         if (st != PCG_OK) return st;
@@ -461,6 +505,8 @@ pcg_status pcg_adjoint(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const
     if (mode != PCG_ADJ_SOLVE && mode != PCG_ADJ_DRAW) return set_error(ctx, PCG_BADARG, "bad adjoint mode");
     if (ctx->unshrunk_q1 > 0)
         return set_error(ctx, PCG_BADARG, "the adjoint takes no unshrunk coefficients (pcg_set_unshrunk)");
+    if (ctx->opt.warm_start)
+        return set_error(ctx, PCG_BADARG, "the adjoint's solve starts from 0 (warm_start must be off)");
     if (!g_logtau || !iters || !resid) return set_error(ctx, PCG_BADARG, "NULL host output");
     *g_logtau = 0.0;
     pcg_status st = check_shapes(ctx, Xr, Xc);

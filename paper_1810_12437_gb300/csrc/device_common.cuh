@@ -98,8 +98,13 @@ __device__ __forceinline__ double prior_var(double tau, double lam) {
 __device__ __forceinline__ double desc_d(const DrawDesc *d, int64_t j) {
     return j < d->q1 ? d->ud[j] : prior_prec(d->tau, d->lambda[j]);
 }
-__device__ __forceinline__ double desc_m(const DrawDesc *d, int64_t j) {
+// m_j of the stop rule (Eq. S2, and Sec. S4.3's M for the unshrunk ones) ...
+__device__ __forceinline__ double desc_mstop(const DrawDesc *d, int64_t j) {
     return j < d->q1 ? d->um[j] : prior_var(d->tau, d->lambda[j]);
+}
+// ... and M^-1 of the preconditioner: the same, or the Jacobi 1 / diag(Phi)_j.
+__device__ __forceinline__ double desc_m(const DrawDesc *d, int64_t j) {
+    return d->mj ? d->mj[j] : desc_mstop(d, j);
 }
 __device__ __forceinline__ double desc_prior_term(const DrawDesc *d, int64_t j, double delta) {
     return j < d->q1 ? delta * sqrt(d->ud[j]) : delta / (d->tau * d->lambda[j]);
@@ -111,5 +116,25 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p) { return __ldcs(p
 __device__ __forceinline__ int4 ld_stream4(const int4 *p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ T ld_gather(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// lane-partial gather-sum of one CSR row / CSC column by a group of G lanes;
+// the caller combines the group with group_sum outside any divergent branch.
+// ---------------------------------------------------------------------------
+template <int G, typename T>
+__device__ __forceinline__ T segment_partial(const int32_t *__restrict__ idx, int64_t k0,
+                                                int64_t k1, const T *__restrict__ x, int lane) {
+    T acc = T(0);
+    int64_t k = k0 + lane;
+    for (; k + 3 * G < k1; k += 4 * G) {
+        const int32_t j0 = ld_stream(idx + k), j1 = ld_stream(idx + k + G);
+        const int32_t j2 = ld_stream(idx + k + 2 * G), j3 = ld_stream(idx + k + 3 * G);
+        const T a0 = ld_gather(x + j0), a1 = ld_gather(x + j1);
+        const T a2 = ld_gather(x + j2), a3 = ld_gather(x + j3);
+        acc += (a0 + a1) + (a2 + a3);
+    }
+    for (; k < k1; k += G) acc += ld_gather(x + ld_stream(idx + k));
+    return acc;
+}
 
 }  // namespace pcg

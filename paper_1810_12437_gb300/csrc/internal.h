@@ -61,6 +61,10 @@ struct DrawDesc {
     // (0: flat prior) and preconditioner variance um[j] = gamma_j^2 (device, q1 each)
     int q1;
     const double *ud, *um;
+    // preconditioner M^-1 (device, p): the Jacobi 1 / diag(Phi), or NULL for the
+    // prior preconditioner (the stop rule's weights either way)
+    const double *mj;
+    int warm;              // beta holds beta_0 on entry (Sec. S4.1)
 };
 
 // Device workspace of the single-RHS path (sizes grow on demand).
@@ -72,6 +76,7 @@ struct SingleWs {
     float *om32;                  // n
     double *om64;                 // n (float64 omega for the tiled float64 products)
     float2 *omdf;                 // n (omega as double-float pairs, DF32 mode)
+    double *mj;                   // p (Jacobi preconditioner 1 / diag(Phi))
     double *partials;             // kMaxReduceBlocks * 4
     unsigned int *counters;       // 16
     CgScalars *sc;                // 1
@@ -193,6 +198,12 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
                        const double *omega, const double *z, const double *lambda,
                        const double *tau, const double *eta, const double *delta, double tol,
                        int max_iter, double *beta, int *iters, double *resid, int *status);
+
+// LSQR on the least-squares form (lsqr.cu)
+pcg_status run_lsqr(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *omega,
+                    const double *z, const double *lambda, double tau, const double *eta,
+                    const double *delta, double tol, int max_iter, double *beta, int *iters,
+                    double *resid);
 
 // uneven batch (uneven.cu)
 pcg_status run_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol, int max_iter,

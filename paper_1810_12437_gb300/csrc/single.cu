@@ -25,26 +25,6 @@
 
 namespace pcg {
 
-// ---------------------------------------------------------------------------
-// lane-partial gather-sum of one CSR row / CSC column by a group of G lanes;
-// the caller combines the group with group_sum outside any divergent branch.
-// ---------------------------------------------------------------------------
-template <int G, typename T>
-__device__ __forceinline__ T segment_partial(const int32_t *__restrict__ idx, int64_t k0,
-                                                int64_t k1, const T *__restrict__ x, int lane) {
-    T acc = T(0);
-    int64_t k = k0 + lane;
-    for (; k + 3 * G < k1; k += 4 * G) {
-        const int32_t j0 = ld_stream(idx + k), j1 = ld_stream(idx + k + G);
-        const int32_t j2 = ld_stream(idx + k + 2 * G), j3 = ld_stream(idx + k + 3 * G);
-        const T a0 = ld_gather(x + j0), a1 = ld_gather(x + j1);
-        const T a2 = ld_gather(x + j2), a3 = ld_gather(x + j3);
-        acc += (a0 + a1) + (a2 + a3);
-    }
-    for (; k < k1; k += G) acc += ld_gather(x + ld_stream(idx + k));
-    return acc;
-}
-
 __device__ __forceinline__ bool gate_closed(const int *done, const int *need) {
     return *(volatile const int *)done || (need && !*(volatile const int *)need);
 }
@@ -84,20 +64,24 @@ __global__ void k_t_fin_out(const DrawDesc *__restrict__ d, TiledArgs A, const d
 
 // ---------------------------------------------------------------------------
 // a1 + a2: b_j = sum_{i in col j} w_i + delta_j / (tau lambda_j)  (or the given
-// right-hand side), then beta = 0, r = b, z = m b, s = z, rho_0 = r.z.
+// right-hand side), then beta = 0, r = b, z = M^-1 b, s = z, rho_0 = r.z, and
+// the stop rule's reference rho_b = ||tau lambda (.) b||^2 (Eq. S2; equal to
+// rho_0 under the prior preconditioner).  With a warm start (Sec. S4.1) only b
+// and rho_b are formed here: k_warm_init sets r, s and rho from beta_0.
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d,
                                                   const double *__restrict__ w, SingleWs ws) {
     __shared__ double red[32];
-    __shared__ double sums[1];
+    __shared__ double sums[2];
     const int64_t p = d->p;
     const int lane = threadIdx.x & (G - 1);
     const int64_t gpw = 32 / G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t sub = (threadIdx.x & 31) / G;
-    double rho = 0.0;
+    const bool warm = d->warm != 0;
+    double rho = 0.0, rho_b = 0.0;
     for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
         const int64_t j = base + sub;
         double acc = 0.0;
@@ -106,22 +90,28 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
         acc = group_sum<G>(acc);
         if (j < p && lane == 0) {
             const double b = d->rhs ? d->rhs[j] : acc + desc_prior_term(d, j, d->delta[j]);
-            const double z = desc_m(d, j) * b;
+            const double tb = b * (desc_mstop(d, j) * b);
             ws.b[j] = b;
-            ws.r[j] = b;
-            ws.s64[j] = z;
-            ws.s32[j] = (float)z;
-            if (d->df) ws.sdf[j] = df_from_double(z);
-            d->beta[j] = 0.0;
-            rho += b * z;
+            rho_b += tb;
+            if (!warm) {
+                const double z = desc_m(d, j) * b;
+                ws.r[j] = b;
+                ws.s64[j] = z;
+                ws.s32[j] = (float)z;
+                if (d->df) ws.sdf[j] = df_from_double(z);
+                d->beta[j] = 0.0;
+                rho += d->mj ? b * z : tb;
+            }
         }
     }
-    const double tot = block_sum(rho, red);
-    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 0, sums, red) && threadIdx.x == 0) {
+    double tot[2];
+    tot[0] = block_sum(rho, red);
+    tot[1] = block_sum(rho_b, red);
+    if (grid_reduce<2>(tot, ws.partials, ws.counters + 0, sums, red) && threadIdx.x == 0) {
         CgScalars *sc = ws.sc;
-        const double r0 = sums[0];
+        const double r0 = sums[0], rb = sums[1];
         sc->rho = r0;
-        sc->rho0 = r0;
+        sc->rho0 = rb;
         sc->rho_prev = r0;
         sc->sigma = 0.0;
         sc->alpha = 0.0;
@@ -130,11 +120,14 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
         sc->need_ru = 0;
         sc->pending = 0;
         sc->ru_trips = 0;
-        sc->resid = stop_quantity(d->stop_rule, r0, r0, p);
-        if (!isfinite(r0)) {
+        sc->resid = stop_quantity(d->stop_rule, rb, rb, p);
+        if (!isfinite(rb) || !isfinite(r0)) {
             sc->status = PCG_NONFINITE;
             sc->done = 1;
-        } else if (stop_met(d->stop_rule, r0, r0, p, d->tol)) {
+        } else if (warm) {
+            sc->status = kRunning;   // decided by k_warm_init
+            sc->done = 0;
+        } else if (stop_met(d->stop_rule, rb, rb, p, d->tol)) {
             sc->status = PCG_OK;
             sc->done = 1;
         } else if (d->max_iter <= 0) {
@@ -143,6 +136,82 @@ __global__ void __launch_bounds__(256) k_rhs_init(const DrawDesc *__restrict__ d
         } else {
             sc->status = kRunning;
             sc->done = 0;
+        }
+    }
+}
+
+// Jacobi preconditioner (Sec. 2.4): M^-1_j = 1 / diag(Phi)_j with
+// diag(Phi)_j = sum_{i in col j} omega_i + d_j for binary X (float64).
+template <int G>
+__global__ void __launch_bounds__(256) k_jacobi(const DrawDesc *__restrict__ d, double *__restrict__ mj) {
+    const int64_t p = d->p;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        double acc = 0.0;
+        if (j < p)
+            acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], d->omega, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) mj[j] = 1.0 / (acc + desc_d(d, j));
+    }
+}
+
+// Warm start (Sec. S4.1): with u64 = Omega X beta_0 (float64), r_0 = b -
+// (X^T u64 + d beta_0), z = M^-1 r_0, s = z, rho = r.z; stop test on
+// ||tau lambda (.) r_0||^2 against rho_b (set by k_rhs_init).
+template <int G>
+__global__ void __launch_bounds__(256) k_warm_init(const DrawDesc *__restrict__ d,
+                                                   const double *__restrict__ u64, SingleWs ws) {
+    __shared__ double red[32];
+    __shared__ double sums[2];
+    CgScalars *sc = ws.sc;
+    if (*(volatile const int *)&sc->done) return;
+    const int64_t p = d->p;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t sub = (threadIdx.x & 31) / G;
+    double rho = 0.0, rho_s = 0.0;
+    for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
+        const int64_t j = base + sub;
+        double acc = 0.0;
+        if (j < p)
+            acc = segment_partial<G, double>(d->row_idx, d->col_ptr[j], d->col_ptr[j + 1], u64, lane);
+        acc = group_sum<G>(acc);
+        if (j < p && lane == 0) {
+            const double rj = ws.b[j] - (acc + desc_d(d, j) * d->beta[j]);
+            const double z = desc_m(d, j) * rj;
+            ws.r[j] = rj;
+            ws.s64[j] = z;
+            ws.s32[j] = (float)z;
+            if (d->df) ws.sdf[j] = df_from_double(z);
+            const double t = rj * z;
+            rho += t;
+            rho_s += d->mj ? rj * (desc_mstop(d, j) * rj) : t;
+        }
+    }
+    double tot[2];
+    tot[0] = block_sum(rho, red);
+    tot[1] = block_sum(rho_s, red);
+    if (grid_reduce<2>(tot, ws.partials, ws.counters + 4, sums, red) && threadIdx.x == 0) {
+        const double r0 = sums[0], rs = sums[1];
+        sc->rho = r0;
+        sc->rho_prev = r0;
+        sc->resid = stop_quantity(d->stop_rule, rs, sc->rho0, p);
+        if (!isfinite(r0) || !isfinite(rs)) {
+            sc->status = PCG_NONFINITE;
+            sc->done = 1;
+        } else if (stop_met(d->stop_rule, rs, sc->rho0, p, d->tol)) {
+            sc->status = PCG_OK;
+            sc->done = 1;
+        } else if (d->max_iter <= 0) {
+            sc->status = PCG_MAXITER;
+            sc->done = 1;
         }
     }
 }
@@ -231,7 +300,7 @@ __global__ void __launch_bounds__(256) k_csc(const DrawDesc *__restrict__ d,
 __global__ void __launch_bounds__(256) k_update(const DrawDesc *__restrict__ d, SingleWs ws,
                                                 cudaGraphConditionalHandle h_ru, int use_cond) {
     __shared__ double red[32];
-    __shared__ double sums[1];
+    __shared__ double sums[2];
     CgScalars *sc = ws.sc;
     if (*(volatile const int *)&sc->done) {
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_ru, 0);
@@ -239,29 +308,34 @@ __global__ void __launch_bounds__(256) k_update(const DrawDesc *__restrict__ d, 
     }
     const int64_t p = d->p;
     const double alpha = sc->alpha;
-    double rho = 0.0;
+    double rho = 0.0, rho_s = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double bj = d->beta[j] + alpha * ws.s64[j];
         const double rj = ws.r[j] - alpha * ws.v64[j];
         d->beta[j] = bj;
         ws.r[j] = rj;
-        rho += rj * (desc_m(d, j) * rj);
+        const double t = rj * (desc_m(d, j) * rj);
+        rho += t;
+        rho_s += d->mj ? rj * (desc_mstop(d, j) * rj) : t;
     }
-    const double tot = block_sum(rho, red);
-    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 2, sums, red) && threadIdx.x == 0) {
-        const double rn = sums[0];
+    double tot[2];
+    tot[0] = block_sum(rho, red);
+    tot[1] = block_sum(rho_s, red);
+    if (grid_reduce<2>(tot, ws.partials, ws.counters + 2, sums, red) && threadIdx.x == 0) {
+        const double rn = sums[0], rs = sums[1];
         sc->iter += 1;
-        if (!isfinite(rn)) {
+        if (!isfinite(rn) || !isfinite(rs)) {
             sc->status = PCG_NONFINITE;
             sc->done = 1;
             sc->need_ru = 0;
         } else {
-            const bool conv = stop_met(d->stop_rule, rn, sc->rho0, p, d->tol);
+            // the stop rule on ||tau lambda (.) r||^2 (Eq. S2), whatever M is
+            const bool conv = stop_met(d->stop_rule, rs, sc->rho0, p, d->tol);
             sc->rho_prev = sc->rho;
             sc->rho = rn;
             sc->gamma = rn / sc->rho_prev;
-            sc->resid = stop_quantity(d->stop_rule, rn, sc->rho0, p);
+            sc->resid = stop_quantity(d->stop_rule, rs, sc->rho0, p);
             if (d->refined) {
                 const bool periodic = d->reliable_k > 0 && (sc->iter % d->reliable_k) == 0;
                 sc->pending = conv ? 1 : 0;
@@ -293,7 +367,7 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
                                                     const double *__restrict__ u64, SingleWs ws,
                                                     int gated) {
     __shared__ double red[32];
-    __shared__ double sums[1];
+    __shared__ double sums[2];
     CgScalars *sc = ws.sc;
     if (gated && gate_closed(&sc->done, &sc->need_ru)) return;
     const int64_t p = d->p;
@@ -302,7 +376,7 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t sub = (threadIdx.x & 31) / G;
-    double rho = 0.0;
+    double rho = 0.0, rho_s = 0.0;
     for (int64_t base = warp * gpw; base < p; base += nwarps * gpw) {
         const int64_t j = base + sub;
         double acc = 0.0;
@@ -313,22 +387,26 @@ __global__ void __launch_bounds__(256) k_true_resid(const DrawDesc *__restrict__
             const double bj = d->beta[j];
             const double rj = ws.b[j] - (acc + desc_d(d, j) * bj);
             ws.r[j] = rj;
-            rho += rj * (desc_m(d, j) * rj);
+            const double t = rj * (desc_m(d, j) * rj);
+            rho += t;
+            rho_s += d->mj ? rj * (desc_mstop(d, j) * rj) : t;
         }
     }
-    const double tot = block_sum(rho, red);
-    if (grid_reduce<1>(&tot, ws.partials, ws.counters + 3, sums, red) && threadIdx.x == 0) {
-        const double rt = sums[0];
+    double tot[2];
+    tot[0] = block_sum(rho, red);
+    tot[1] = block_sum(rho_s, red);
+    if (grid_reduce<2>(tot, ws.partials, ws.counters + 3, sums, red) && threadIdx.x == 0) {
+        const double rt = sums[0], rts = sums[1];
         sc->need_ru = 0;
-        if (!isfinite(rt)) {
+        if (!isfinite(rt) || !isfinite(rts)) {
             sc->status = PCG_NONFINITE;
             sc->done = 1;
         } else {
             sc->rho = rt;
             sc->gamma = rt / sc->rho_prev;
-            sc->resid = stop_quantity(d->stop_rule, rt, sc->rho0, p);
+            sc->resid = stop_quantity(d->stop_rule, rts, sc->rho0, p);
             if (sc->pending) {
-                if (stop_met(d->stop_rule, rt, sc->rho0, p, d->tol)) {
+                if (stop_met(d->stop_rule, rts, sc->rho0, p, d->tol)) {
                     sc->status = PCG_OK;
                     sc->done = 1;
                 } else {
@@ -445,6 +523,16 @@ static void *true_resid_ptr(int G) {
     PCG_DISPATCH_G(G, f = (void *)k_true_resid<GG>);
     return f;
 }
+static void *jacobi_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_jacobi<GG>);
+    return f;
+}
+static void *warm_init_ptr(int G) {
+    void *f = nullptr;
+    PCG_DISPATCH_G(G, f = (void *)k_warm_init<GG>);
+    return f;
+}
 
 pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     if (n <= ctx->cap_n && p <= ctx->cap_p && ctx->ws.sc) return PCG_OK;
@@ -470,7 +558,7 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     const size_t szp64 = up(sizeof(double) * cp), szp32 = up(sizeof(float) * cp);
     const size_t szn32 = up(sizeof(float) * cn), szn64 = up(sizeof(double) * cn);
     const size_t szpart = up(sizeof(double) * kMaxReduceBlocks * 4);
-    const size_t total = 5 * szp64 + szp32 + szn32 + 2 * szn64 + szpart + up(64 * sizeof(unsigned)) +
+    const size_t total = 6 * szp64 + szp32 + szn32 + 2 * szn64 + szpart + up(64 * sizeof(unsigned)) +
                          up(sizeof(CgScalars)) + up(sizeof(DrawDesc));
     char *base = nullptr;
     PCG_CUDA_TRY(ctx, cudaMalloc(&base, total));
@@ -487,6 +575,7 @@ pcg_status ensure_single_ws(pcg_ctx *ctx, int64_t n, int64_t p) {
     w.om32 = (float *)take(szn32);
     w.om64 = (double *)take(szn64);
     w.omdf = (float2 *)take(szn64);
+    w.mj = (double *)take(szp64);
     w.partials = (double *)take(szpart);
     w.counters = (unsigned *)take(up(64 * sizeof(unsigned)));
     w.sc = (CgScalars *)take(up(sizeof(CgScalars)));
@@ -549,6 +638,7 @@ struct NodeArgs {
     float2 *omdf;
     const void *om_t, *s_t;
     void *pc;
+    double *mj;
 };
 
 static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, const TiledPlan &tp,
@@ -601,9 +691,27 @@ static pcg_status build_graph(pcg_ctx *ctx, const DrawDesc &d, int precision, co
         void *args[] = {&A.d, &A.w64, &A.om32, &A.want_w, &A.want_om32, &A.om64, &A.omdf};
         e = add_kernel(g, &n_w, nullptr, 0, (void *)k_rhs_w, L.grid_stream, L.threads, args);
     }
+    cudaGraphNode_t pre = n_w;
+    if (e == cudaSuccess && d.mj) {   // Jacobi preconditioner, before any use of M^-1
+        cudaGraphNode_t n_j;
+        A.mj = ctx->ws.mj;
+        void *args[] = {&A.d, &A.mj};
+        e = add_kernel(g, &n_j, &pre, 1, jacobi_ptr(L.G_col), L.grid_stream, L.threads, args);
+        pre = n_j;
+    }
     if (e == cudaSuccess) {
         void *args[] = {&A.d, &A.w64, &A.ws};
-        e = add_kernel(g, &n_init, &n_w, 1, rhs_init_ptr(L.G_col), L.grid_stream, L.threads, args);
+        e = add_kernel(g, &n_init, &pre, 1, rhs_init_ptr(L.G_col), L.grid_stream, L.threads, args);
+    }
+    if (e == cudaSuccess && d.warm) {   // r_0 = b - Phi beta_0 (float64 product on beta_0)
+        cudaGraphNode_t n_wc = nullptr, n_wi = nullptr;
+        void *a1[] = {&A.d, &A.nulld, &A.nulld, &A.w64, &A.done, &A.nulli};
+        e = add_kernel(g, &n_wc, &n_init, 1, csr_kernel_ptr<double>(L.G_row), L.grid_stream, L.threads, a1);
+        if (e == cudaSuccess) {
+            void *a2[] = {&A.d, &A.u64, &A.ws};
+            e = add_kernel(g, &n_wi, &n_wc, 1, warm_init_ptr(L.G_col), L.grid_stream, L.threads, a2);
+        }
+        n_init = n_wi;
     }
     if (e == cudaSuccess)
         e = cudaGraphConditionalHandleCreate(&A.h_while, g, 1, cudaGraphCondAssignDefault);
@@ -715,8 +823,16 @@ static pcg_status run_plain(pcg_ctx *ctx, const DrawDesc &d, int precision, cons
     PCG_PROF(ctx, "rhs_w", k_rhs_w<<<L.grid_stream, B, 0, st>>>(dd, (double *)ws.u, ws.om32, d.rhs == nullptr, f32,
                                                                 (tp.valid && !f32 && !df) ? ws.om64 : nullptr,
                                                                 (tp.valid && df) ? ws.omdf : nullptr));
+    if (d.mj)
+        PCG_PROF(ctx, "jacobi", PCG_DISPATCH_G(L.G_col, (k_jacobi<GG><<<L.grid_stream, B, 0, st>>>(dd, ws.mj))));
     PCG_PROF(ctx, "rhs_init", PCG_DISPATCH_G(L.G_col, (k_rhs_init<GG><<<L.grid_stream, B, 0, st>>>(dd, (const double *)ws.u, ws))));
     const int *done = &ws.sc->done, *need = &ws.sc->need_ru;
+    if (d.warm) {
+        PCG_PROF(ctx, "warm_csr_f64", PCG_DISPATCH_G(L.G_row, (k_csr<double, GG><<<L.grid_stream, B, 0, st>>>(
+                                       dd, nullptr, nullptr, (double *)ws.u, done, nullptr))));
+        PCG_PROF(ctx, "warm_init", PCG_DISPATCH_G(L.G_col, (k_warm_init<GG><<<L.grid_stream, B, 0, st>>>(
+                                    dd, (const double *)ws.u, ws))));
+    }
     for (int it = 0;; it += 8) {
         for (int k = 0; k < 8; ++k) {
             if (tp.valid) {
@@ -782,6 +898,7 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
     d.refined = (precision == PCG_PREC_FP32_REFINED) ? 1 : 0;
     d.reliable_k = ctx->opt.reliable_k;
     d.df = prec_pairs(precision) ? 1 : 0;
+    d.mj = ctx->opt.preconditioner == PCG_PRECOND_JACOBI ? ctx->ws.mj : nullptr;
     st = with_unshrunk(ctx, d);
     if (st != PCG_OK) return st;
     *ctx->h_desc = d;
@@ -800,9 +917,9 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         // shapes (never a caller pointer: those are read from the descriptor).
         const SingleLaunch L = single_launch(ctx, d);
         char key[256];
-        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d|%d:%016llx",
-                 L.G_row, L.G_col, L.grid_stream, L.grid_vec, precision, d.refined, mode, (int)tp.valid,
-                 (unsigned long long)(tp.valid ? plan_fingerprint(tp) : 0ull));
+        snprintf(key, sizeof key, "single:%d:%d:%d:%d:%d:%d:%d:%d:%d|%d:%016llx",
+                 L.G_row, L.G_col, L.grid_stream, L.grid_vec, precision, d.refined, mode, d.mj ? 1 : 0,
+                 d.warm, (int)tp.valid, (unsigned long long)(tp.valid ? plan_fingerprint(tp) : 0ull));
         // n and p enter through the plan only when it is valid
         std::string skey = std::string(key) + (tp.valid ? ":" + std::to_string(tp.n) + ":" + std::to_string(tp.p) : "");
         auto it = ctx->named_graphs.find(skey);
@@ -818,11 +935,12 @@ pcg_status run_single(pcg_ctx *ctx, const DrawDesc &din, int precision, int mode
         PCG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_sc, ctx->ws.sc, sizeof(CgScalars),
                                           cudaMemcpyDeviceToHost, ctx->stream));
         PCG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        // graph nodes that ran: 2 set-up kernels, per loop trip (at least one)
+        // graph nodes that ran: 2 set-up kernels (+1 Jacobi, +2 warm start), per loop trip (at least one)
         // 4 (untiled) or 6 (tiled: csr, u, csc, finalize, update, direction),
         // 2 per float64 recomputation of r
         const CgScalars &h = *ctx->h_sc;
-        ctx->last_launches += 2 + (tp.valid ? 6 : 4) * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
+        ctx->last_launches += 2 + (d.mj ? 1 : 0) + (d.warm ? 2 : 0) +
+                              (tp.valid ? 6 : 4) * (int64_t)std::max(h.iter, 1) + 2 * (int64_t)h.ru_trips;
     } else {
         st = run_plain(ctx, d, precision, tp);
         if (st != PCG_OK) return st;

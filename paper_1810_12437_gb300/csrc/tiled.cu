@@ -553,15 +553,43 @@ static uint64_t fnv_mix(uint64_t h, uint64_t v) {
     return h;
 }
 
+bool tiled_geometry(int64_t n, int64_t p, int64_t nnz, int RG, int vsize, int *W_c, int *T_c, int *W_r,
+                    int *T_r) {
+    if (n <= 0 || p <= 0 || nnz <= 0 || RG <= 0 || vsize <= 0) return false;
+    if (n >= (int64_t)INT32_MAX || p >= (int64_t)INT32_MAX) return false;
+    int64_t w = (kTileSmemBytes - RG * vsize) / (RG * vsize);   // one slot is the zero sentinel
+    w = std::min<int64_t>(w, 65528);
+    w &= ~int64_t(7);
+    if (w < 8) return false;
+    // as few tiles (strips) as fit, then equal widths (a multiple of 8), so that
+    // the last one is not a small remainder whose CTAs idle while the others work
+    auto balanced = [&](int64_t len, int *W, int *T) {
+        const int64_t t = (len + std::min(w, len) - 1) / std::min(w, len);
+        *T = (int)t;
+        *W = (int)(t == 1 ? len : std::min<int64_t>(w, ((len + t - 1) / t + 7) & ~int64_t(7)));
+    };
+    balanced(p, W_c, T_c);
+    balanced(n, W_r, T_r);
+    // Each side keeps every entry's padded position in 32 bits (at most 7 pad
+    // slots for each of the T x nseg segments, the sentinel chunk after them:
+    // the allocation plan_side makes) and counts its segments, and one bound
+    // per segment and tile boundary, in int (the sorts and scans).
+    auto fits = [&](int64_t T, int64_t nseg) {
+        const int64_t nts = T * nseg;
+        const int64_t cap = ((nnz + 7 * nts + 7) & ~int64_t(7)) + 8;
+        return (T + 1) * nseg < (int64_t)INT32_MAX && cap < (int64_t)0xfffffff0ll;
+    };
+    return fits(*T_c, n) && fits(*T_r, p);
+}
+
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
                             int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl) {
     *pl = TiledPlan{};
     const int vsize = vtype == kVtF32 ? 4 : 8;   // staged bytes per value (DF: two floats; FX: int64)
     pl->vtype = vtype;
     const int64_t n = Xr->n, p = Xr->p, nnz = Xr->nnz;
-    // positions are 32-bit inside the kernels (padding included)
-    if (n <= 0 || p <= 0 || nnz <= 0 || nnz + 8 * (n + p) * 4 >= (int64_t)0xfffffff0ll) return PCG_OK;
-    if (n >= (int64_t)INT32_MAX || p >= (int64_t)INT32_MAX) return PCG_OK;
+    int Wc = 0, Tc = 0, Wr = 0, Tr = 0;
+    if (!tiled_geometry(n, p, nnz, RG, vsize, &Wc, &Tc, &Wr, &Tr)) return PCG_OK;   // untiled products
     // A plan depends on the design alone (and on RG, the value type and the
     // groups): reuse the one built for this tag when nothing it depends on has
     // changed, the design's content included (hashed on the device: about one
@@ -599,23 +627,16 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
         }
         ctx->plan_cache.erase(tag);   // rebuilt below under the same buffer names
     }
-    int64_t w = (kTileSmemBytes - RG * vsize) / (RG * vsize);   // one slot is the zero sentinel
-    w = std::min<int64_t>(w, 65528);
-    w &= ~int64_t(7);
     pl->RG = RG;
     pl->vsize = vsize;
     pl->ngroups = std::max(1, ngroups);
     pl->n = n;
     pl->p = p;
     pl->nnz = nnz;
-    // as few tiles (strips) as fit, then equal widths (a multiple of 8), so that
-    // the last one is not a small remainder whose CTAs idle while the others work
-    auto balanced = [&](int64_t len, int *W, int *T) {
-        *T = (int)((len + std::min(w, len) - 1) / std::min(w, len));
-        *W = (int)(*T == 1 ? len : std::min<int64_t>(w, ((len + *T - 1) / *T + 7) & ~int64_t(7)));
-    };
-    balanced(p, &pl->W_c, &pl->T_c);
-    balanced(n, &pl->W_r, &pl->T_r);
+    pl->W_c = Wc;
+    pl->T_c = Tc;
+    pl->W_r = Wr;
+    pl->T_r = Tr;
     // launch shapes: per group one wave of CTAs over the tiles (strips)
     const size_t smem_c = (size_t)(pl->W_c + 1) * RG * vsize, smem_r = (size_t)(pl->W_r + 1) * RG * vsize;
     const int occ_c = std::max(1, std::min(2, (int)(kSmemPerSm / (smem_c + 2048))));

@@ -78,12 +78,18 @@ inline int tiled_u_blocks(const TiledPlan &pl, int num_sms) {
     return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
+// Tile widths and counts of the tiled products for a design of this shape
+// (RG values of vsize bytes staged per column or row); false when the tiled
+// products do not apply: empty X, or more padded positions or segments than
+// the plan's 32-bit positions and int counts hold.
+bool tiled_geometry(int64_t n, int64_t p, int64_t nnz, int RG, int vsize, int *W_c, int *T_c, int *W_r,
+                    int *T_r);
+
 // Builds (on the context stream) the 16-bit index copies, tile bounds and
 // per-warp work split of X for RG values of type vtype per gather and
 // `ngroups` RHS groups; with many_products also the bank-aware entry order
 // (worth its cost only when the plan serves many products).  Leaves
-// pl->valid false when the tiled products do not apply (empty X or nnz beyond
-// 32-bit offsets).
+// pl->valid false when the tiled products do not apply (tiled_geometry).
 pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, const pcg_csc *Xc,
                             int RG, int vtype, int ngroups, bool many_products, TiledPlan *pl);
 TiledKernels tiled_kernels(const TiledPlan &pl);

@@ -563,7 +563,8 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
     // mode runs as float32 with float64 recomputation of r
     G.refined = (ctx->opt.precision == PCG_PREC_FP32_REFINED || prec_pairs(ctx->opt.precision)) ? 1 : 0;
     G.reliable_k = ctx->opt.reliable_k;
-    G.idle_limit_ns = 2000000000ll;   // 2 s without any completed tile anywhere
+    // give up after this long without any completed tile anywhere
+    G.idle_limit_ns = (long long)llround(ctx->opt.idle_limit_s * 1e9);
     *hg = G;
     cudaStream_t s = ctx->stream;
     PCG_CUDA_TRY(ctx, cudaMemcpyAsync(pl.d_probs, hp, sizeof(UProb) * nprob, cudaMemcpyHostToDevice, s));
@@ -571,9 +572,14 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
     PCG_CUDA_TRY(ctx, cudaMemsetAsync(pl.d_state, 0, sizeof(UState) * nprob, s));   // all at PH_W, count 0
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms_out) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, s);
+        cudaError_t ce = cudaEventCreate(&e0);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        if (ce != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            return cuda_error(ctx, ce, "timing an autotune candidate");
+        }
     }
     std::string key = std::string("uneven_graph:") + (f32 ? "f" : "d") + ":" + std::to_string(pl.grid) +
                       ":" + std::to_string(nprob) + ":" + std::to_string((uintptr_t)pl.d_probs) + ":" +
@@ -610,14 +616,17 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
                  (f32 ? k_uneven<float><<<pl.grid, 256, 0, s>>>(pl.d_probs, pl.d_state, pl.d_glob, nprob)
                       : k_uneven<double><<<pl.grid, 256, 0, s>>>(pl.d_probs, pl.d_state, pl.d_glob, nprob)));
     }
-    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    cudaError_t le = cudaGetLastError();
     if (ms_out) {
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(ms_out, e0, e1);
+        cudaError_t ce = le;
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms_out, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (ce != cudaSuccess) return cuda_error(ctx, ce, "timing an autotune candidate");
     }
+    PCG_CUDA_TRY(ctx, le);
     return PCG_OK;
 }
 

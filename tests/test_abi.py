@@ -87,3 +87,24 @@ def test_precision_names_match_header():
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pcg_beta.h")).read()
     enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"PCG_PREC_(\w+)\s*=\s*(\d+)", hdr)}
     assert enum == PREC
+
+
+def test_tiled_geometry_and_size_guard(lib):
+    """pcg_tiled_plan_applies (host arithmetic): the bench workload's tile and
+    strip counts, and the size guard on the plan's 32-bit padded positions
+    and int segment counts.  n = 1e8 rows with p = 5e4 and 1e9 nonzeros
+    passes the former test nnz + 32 (n + p) < 2^32; with one double-float
+    right-hand side per group it has 2 column tiles and fits, but with 4 its
+    CSR side has 8 column tiles, 8e8 (tile, row) segments, and 7 pad slots
+    for each of them overflow 32-bit positions: the untiled products must
+    take it."""
+    import paper_1810_12437_gb300 as pb
+    assert pb.pcg_tiled_plan_applies(500_000, 50_000, 114_693_671, "df32", 2) == (4, 36)
+    assert pb.pcg_tiled_plan_applies(500_000, 50_000, 114_693_671, "df32", 1) == (2, 18)
+    assert pb.pcg_tiled_plan_applies(500_000, 50_000, 114_693_671, "fp32", 1) == (1, 9)
+    n, p, nnz = 100_000_000, 50_000, 1_000_000_000
+    assert nnz + 32 * (n + p) < 2 ** 32
+    assert pb.pcg_tiled_plan_applies(n, p, nnz, "df32", 1) == (2, 3553)
+    assert pb.pcg_tiled_plan_applies(n, p, nnz, "df32", 4) is None
+    assert pb.pcg_tiled_plan_applies(0, 10, 0, "df32", 1) is None
+    assert pb.pcg_tiled_plan_applies(10, 10, 5, "df32", 0) is None

@@ -1,9 +1,10 @@
 """Parity of the batched path (R chains sharing X, one RHS-block product per
 iteration) with the CPU oracle run chain by chain, and with the single-RHS
 path.  Tolerances as for the single path: relative L2 1e-5 in the refined
-mode, 1e-3 in pure float32; iteration counts within the float32 inflation
-bound against the oracle, and within 30% of the single-RHS float32 path
-(same arithmetic, different summation order)."""
+mode, 1e-3 in pure float32; iteration counts within the window of
+tests/iteration_band.py (the oracle's band at the same storage precision),
+and within 30% of the single-RHS float32 path (same arithmetic, different
+summation order)."""
 import numpy as np
 import pytest
 import torch
@@ -11,6 +12,7 @@ import torch
 from oracle import oracle as O
 from paper_1810_12437_gb300 import inputs
 from tests.gpu_helpers import T, dev, need_gpu, rel
+from tests.iteration_band import problem_window
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +53,8 @@ def test_batched_matches_oracle_per_chain(pb, small3, prec, bound):
         om, z, lam, tau, eta, delta = chain(P, r)
         ref, k, _, st = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
         assert res.status[r] == pb.PCG_OK and st == O.OK, (r, res.status[r])
-        assert k - 2 <= res.iters[r] <= 3.5 * k + 10, (r, res.iters[r], k)
+        w = problem_window(prec, P, r)
+        assert w.holds(res.iters[r]), (r, res.iters[r], str(w))
         assert rel(beta[r], ref) < bound, r
 
 
@@ -87,7 +90,8 @@ def test_batched_every_group_width(pb, small3, rg, monkeypatch):
     for r in (0, 5, 11, 15):
         om, z, lam, tau, eta, delta = chain(P, r)
         ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
-        assert res.status[r] == pb.PCG_OK and k - 2 <= res.iters[r] <= 3.5 * k + 10, (r, res.iters[r], k)
+        w = problem_window("fp32_refined", P, r)
+        assert res.status[r] == pb.PCG_OK and w.holds(res.iters[r]), (r, res.iters[r], str(w))
         assert rel(beta[r], ref) < 1e-5, r
 
 
@@ -107,7 +111,8 @@ def test_batched_graph_and_plain_agree(pb, small3):
 @pytest.mark.parametrize("prec", ["df32", "fx64"])
 def test_batched_pair_products_match_oracle(pb, small3, prec):
     """Double-float and fixed-point products in the batched path: per chain,
-    iteration counts in the float64 band of the oracle's and draws within 1e-5."""
+    iteration counts within 2 of the oracle's float-pair band and draws
+    within 1e-5."""
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
     ctx = pb.Context(precision=prec)
@@ -116,7 +121,8 @@ def test_batched_pair_products_match_oracle(pb, small3, prec):
     for r in range(16):
         om, z, lam, tau, eta, delta = chain(P, r)
         ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
-        assert res.status[r] == pb.PCG_OK and abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (r, res.iters[r], k)
+        w = problem_window(prec, P, r)
+        assert res.status[r] == pb.PCG_OK and w.holds(res.iters[r]), (r, res.iters[r], str(w))
         assert rel(beta[r], ref) < 1e-5, r
 
 
@@ -124,18 +130,19 @@ def test_batched_pair_products_match_oracle(pb, small3, prec):
 @pytest.mark.parametrize("rg", ["1", "2", "4"])
 def test_batched_pair_products_every_group_width(pb, small3, rg, prec, monkeypatch):
     """Double-float and fixed-point products in groups of 1, 2 and 4
-    right-hand sides (one launch covers every group): per chain, float64-band
-    iteration counts and draws within 1e-5 of the oracle."""
+    right-hand sides (one launch covers every group): per chain, iteration
+    counts within 2 of the oracle's float-pair band and draws within 1e-5."""
     monkeypatch.setenv("PCG_BETA_BATCH_RG", rg)
     P = small3
     X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
     ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
     beta = res.beta.cpu().numpy()
-    for r in (0, 3, 8, 15):
+    for r in (0, 2, 3, 8, 9, 15):
         om, z, lam, tau, eta, delta = chain(P, r)
         ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
-        assert res.status[r] == pb.PCG_OK and abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (r, res.iters[r], k)
+        w = problem_window(prec, P, r)
+        assert res.status[r] == pb.PCG_OK and w.holds(res.iters[r]), (r, res.iters[r], str(w))
         assert rel(beta[r], ref) < 1e-5, r
 
 
@@ -155,12 +162,13 @@ def test_batched_tail_plan(pb, small3, prec, monkeypatch):
         res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
         runs[flag] = (res, pb.pcg_last_kernel_launches(ctx))
     assert runs["1"][1] > runs["0"][1]
+    wins = [problem_window(prec, P, r) for r in range(16)]
     for flag, (res, _) in runs.items():
         beta = res.beta.cpu().numpy()
         for r in range(16):
             om, z, lam, tau, eta, delta = chain(P, r)
             ref, k, _, _ = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)
-            assert res.status[r] == pb.PCG_OK and abs(res.iters[r] - k) <= max(2, int(0.08 * k)), (flag, r)
+            assert res.status[r] == pb.PCG_OK and wins[r].holds(res.iters[r]), (flag, r, res.iters[r], str(wins[r]))
             assert rel(beta[r], ref) < 1e-5, (flag, r)
 
 
@@ -198,9 +206,9 @@ def test_batched_full_size_pair_products_match_oracle_samples(pb, prec):
     fixed-point products): per chain the status and beta at the oracle's 64
     sampled coordinates (tests/golden/config3_oracle.json, written by a script
     that runs only the oracle) within relative L2 1e-5, the true residual of
-    three chains within the stop rule, and the iteration count within 12 % of
-    the oracle's: on these chains (up to 3,369 iterations) the double-float
-    counts run 3-11 % below the oracle's sequential float64 sums, never above."""
+    three chains within the stop rule, and the iteration count within 2 of
+    the oracle's float-pair band (compensated sums, float-pair storage, on
+    the inputs and on one-ulp perturbations of omega and lambda)."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "config3_oracle.json")) as f:
@@ -213,12 +221,13 @@ def test_batched_full_size_pair_products_match_oracle_samples(pb, prec):
     res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=20_000)
     beta = res.beta.cpu().numpy()
     for g in gold["chains"]:
-        r, k = g["chain"], g["iters"]
+        r = g["chain"]
         idx = np.asarray(g["sample_idx"])
         ref = np.asarray(g["beta_sample"])
         assert res.status[r] == pb.PCG_OK, r
         assert rel(beta[r][idx], ref) < 1e-5, r
-        assert abs(res.iters[r] - k) <= max(2, int(0.12 * k)), (r, res.iters[r], k)
+        band = [gold[key][r]["iters"] for key in ("f32x2", "f32x2_ulp")]
+        assert min(band) - 2 <= res.iters[r] <= max(band) + 2, (r, res.iters[r], band)
     for r in (0, 4, 15):
         om, z, lam, tau, eta, delta = chain(P, r)
         b = O.build_b(P.X, om, z, lam, tau, eta, delta)

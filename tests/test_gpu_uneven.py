@@ -7,6 +7,7 @@ import torch
 from oracle import oracle as O
 from paper_1810_12437_gb300 import inputs
 from tests.gpu_helpers import T, dev, need_gpu, rel
+from tests.iteration_band import problem_window
 
 pytestmark = pytest.mark.gpu
 
@@ -44,19 +45,18 @@ def test_uneven_matches_oracle(pb, prec, bound):
     probs = small_batch()
     ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_uneven(ctx, [as_device(pb, P) for P in probs], tol=1e-6, max_iter=20_000)
+    # the persistent kernel's products are float64 or float32: the double-float
+    # and fixed-point modes run as float32 refined
+    mode = prec if prec in ("fp64", "fp32") else "fp32_refined"
     for q, (P, r) in enumerate(zip(probs, res)):
         ref, k, _, st = O.draw_beta_cg(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-6)
         assert r.status == pb.PCG_OK and st == O.OK, q
         beta = r.beta.cpu().numpy()
-        if prec == "fp64":
-            # float64: counts within max(2, 8%) of the oracle's; against the
-            # oracle stopped by the same rule (these half-Cauchy problems are
-            # ill-conditioned, so equal-k iterates amplify rounding)
-            assert abs(r.iters - k) <= max(2, int(0.08 * k)), (q, r.iters, k)
-            assert rel(beta, ref) < bound, q
-        else:
-            assert k - 2 <= r.iters <= 3.5 * k + 10, (q, r.iters, k)
-            assert rel(beta, ref) < bound, q
+        # counts within the window of the oracle's band at the same storage
+        # precision; draws against the oracle stopped by the same rule
+        w = problem_window(mode, P)
+        assert w.holds(r.iters), (q, r.iters, str(w))
+        assert rel(beta, ref) < bound, q
 
 
 def test_uneven_matches_single_path(pb):
@@ -128,4 +128,5 @@ def test_uneven_config4_full(pb):
         assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6, q
         if q in pick:
             ref, k, _, _ = O.draw_beta_cg(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-6)
-            assert k - 2 <= r.iters <= 3.5 * k + 10 and rel(beta, ref) < 1e-5, (q, r.iters, k)
+            w = problem_window("fp32_refined", P)
+            assert w.holds(r.iters) and rel(beta, ref) < 1e-5, (q, r.iters, str(w))
