@@ -72,3 +72,52 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
 def test_job_value_counts_every_rank():
     assert bench.job_value(1, 2000.0) == pytest.approx(bench.NRHS / 2.0)
     assert bench.job_value(4, 2000.0) == pytest.approx(4 * bench.NRHS / 2.0)
+
+
+def test_product_accounting_splits_main_and_tail_plans():
+    """Chains of 3, 1 and 5 iterations at group width 2 with a tail plan:
+    live counts 3, 2, 2, 1, 1 per iteration; the main plan works in the three
+    iterations with two or more chains (groups 2 + 1 + 1, chains 3 + 2 + 2)
+    and the tail plan in the last two."""
+    a = bench.product_accounting([3, 1, 5], 2, tail=True)
+    assert a == {"iterations": 5, "main_iterations": 3, "tail_iterations": 2,
+                 "main_group_units": 4, "main_chain_units": 7, "tail_chain_units": 2}
+    b = bench.product_accounting([3, 1, 5], 2, tail=False)
+    assert b["main_iterations"] == 5 and b["main_group_units"] == 6 and b["tail_iterations"] == 0
+
+
+def test_survey_bytes_share_the_index_streams():
+    """The scope table's bytes: one CSC pass over 16 chains reads the 4-byte
+    row indices once, each chain's vectors once: about 1.04 GB for the two
+    product passes of one 16-chain iteration (the table's 1.09 GB per
+    iteration adds the CG update's vectors)."""
+    one = bench.survey_bytes("bt_csc_df32", N, P, NNZ, 1)
+    sixteen = bench.survey_bytes("bt_csc_df32", N, P, NNZ, 16)
+    assert one == 4 * NNZ + 8 * (P + 1) + 4 * N + 24 * P
+    assert sixteen - one == 15 * (4 * N + 24 * P)
+    both = sixteen + bench.survey_bytes("bt_csr_df32", N, P, NNZ, 16)
+    assert 1.03e9 < both < 1.05e9
+
+
+def test_roofline_counts_only_working_launches():
+    """A profile where the main CSC kernel ran 5 launches (3 working, 2 at its
+    gate) for 6 ms: achieved = scope-table bytes of the 3 working launches
+    over the 6 ms, and avg_launch_us = 6 ms / 3."""
+    acct = bench.product_accounting([3, 1, 5], 2, tail=True)
+    table = {"bt_csc_df32": (6.0, 5), "bt1_csc_df32": (1.0, 5), "b_update": (0.5, 5)}
+    r = bench.roofline(table, acct, N, P, NNZ, 2, 6800.0, "measured")
+    want = (3 * (4 * NNZ + 8 * (P + 1)) + 7 * (4 * N + 24 * P)) / 6e-3 / 1e9
+    assert r["kernel"] == "bt_csc_df32" and r["working_launches"] == 3
+    assert r["achieved"] == pytest.approx(want) and r["frac"] == pytest.approx(want / 6800.0)
+    assert r["avg_launch_us"] == pytest.approx(2000.0)
+    assert r["per_kernel"]["bt1_csc_df32"]["working_launches"] == 2
+
+
+def test_projected_rate_arithmetic(monkeypatch):
+    """Whole draws projected from (rhs seconds, seconds per iteration): two
+    chains of 10 and 30 iterations on one thread take 1 + 10 + 2 + 60 = 73 s."""
+    monkeypatch.setattr(bench, "oracle_iters", lambda P, r, g=None: ([10, 30][r], "test"))
+    rate, _ = bench.projected_rate([(0, 1.0, 1.0), (1, 2.0, 2.0)], 1, None)
+    assert rate == pytest.approx(2 / 73.0)
+    rate2, _ = bench.projected_rate([(0, 1.0, 1.0), (1, 2.0, 2.0)], 2, None)
+    assert rate2 == pytest.approx(2 / 36.5)
