@@ -77,6 +77,14 @@ def _bind(lib):
     lib.oracle_phi_diag.argtypes = [I64, P, P, P, P, D, P]
     lib.oracle_lsqr.argtypes = [I64, I64, P, P, P, P, P, P, P, D, P, P, D, I, I, I, P, P, P]
     lib.oracle_lsqr.restype = I
+    U32, U64 = ctypes.c_uint32, ctypes.c_uint64
+    lib.oracle_philox.argtypes = [P, P, P]
+    lib.oracle_pg_series.argtypes = [D, D, I]
+    lib.oracle_pg_series.restype = D
+    lib.oracle_pg1.argtypes = [I64, P, U64, U32, U32, P]
+    lib.oracle_rng_draws.argtypes = [I, I64, U64, U32, U32, U32, D, P]
+    lib.oracle_gibbs_scales.argtypes = [I64, P, P, P, P, P, U64, U32]
+    lib.oracle_gibbs_omega.argtypes = [I64, I64, P, P, P, P, U64, U32, P, P, P, P]
     lib.oracle_dense_phi.argtypes = [I64, I64, P, P, P, P, D, P]
     lib.oracle_cholesky.argtypes = [I64, P]
     lib.oracle_cholesky.restype = I
@@ -249,6 +257,89 @@ def draw_beta_lsqr(X, omega, z, lam, tau, eta, delta, *, tol=1e-6, stop_rule=STO
                          int(stop_rule), int(max_iter), _SUMS[sums], _p(beta), ctypes.byref(iters),
                          ctypes.byref(resid))
     return beta, iters.value, resid.value, st
+
+
+# ---------------------------------------------------------------------------
+# The rest of the Gibbs cycle of Sec. S1 (horseshoe prior, Polya-Gamma
+# augmentation; see pcg_oracle.c): counter-based random numbers (Philox4x32-10)
+# keyed by a 64-bit seed, one counter per (element, stream, Gibbs step).
+# ---------------------------------------------------------------------------
+STREAM_XI, STREAM_TAU, STREAM_NU, STREAM_LAMBDA, STREAM_OMEGA, STREAM_ETA, STREAM_DELTA = 1, 2, 3, 4, 5, 6, 7
+
+
+def philox(ctr, key):
+    """One Philox4x32-10 block: 4 counter words and 2 key words -> 4 words."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    lib.oracle_philox(_p(c), _p(k), _p(out))
+    return out
+
+
+def pg_series(x, t, terms=60):
+    """The J*(1, 0) density at x by the alternating series of the sampler,
+    in the small-x form (x <= t) or the large-x form (x > t)."""
+    return float(_load().oracle_pg_series(float(x), float(t), int(terms)))
+
+
+def rng_draws(kind, m, seed, index, stream, step, a=1.0):
+    """m successive draws of one counter: kind "uniform", "exp", "normal" or
+    "gamma" (shape a >= 1)."""
+    lib = _load()
+    out = np.empty(m)
+    code = {"uniform": 0, "exp": 1, "normal": 2, "gamma": 3}[kind]
+    lib.oracle_rng_draws(code, m, int(seed), int(index), int(stream), int(step), float(a), _p(out))
+    return out
+
+
+def pg1(c, seed, stream=STREAM_OMEGA, step=0):
+    """PolyaGamma(1, c_k) for each k, element k drawing from counter k."""
+    lib = _load()
+    c = _f64(c)
+    out = np.empty(c.size)
+    lib.oracle_pg1(c.size, _p(c), int(seed), int(stream), int(step), _p(out))
+    return out
+
+
+def gibbs_scales(beta, lam, nu, tau, xi, seed, step):
+    """Steps 1-2 of Sec. S1 (horseshoe, auxiliary nu and xi): returns
+    (lambda, nu, tau, xi) after the update."""
+    lib = _load()
+    beta = _f64(beta)
+    lam, nu = _f64(lam).copy(), _f64(nu).copy()
+    t, x = ctypes.c_double(tau), ctypes.c_double(xi)
+    lib.oracle_gibbs_scales(beta.size, _p(beta), _p(lam), _p(nu), ctypes.byref(t), ctypes.byref(x),
+                            int(seed), int(step))
+    return lam, nu, t.value, x.value
+
+
+def gibbs_omega(X, y, beta, seed, step):
+    """Step 3 of Sec. S1 and step 4's Gaussian vectors: omega ~ PG(1, X beta),
+    z = (y - 1/2) / omega, eta ~ N(0, I_n), delta ~ N(0, I_p)."""
+    lib = _load()
+    y, beta = _f64(y), _f64(beta)
+    omega, z, eta, delta = np.empty(X.n), np.empty(X.n), np.empty(X.n), np.empty(X.p)
+    lib.oracle_gibbs_omega(X.n, X.p, _p(X.row_ptr), _p(X.col_idx), _p(y), _p(beta), int(seed), int(step),
+                           _p(omega), _p(z), _p(eta), _p(delta))
+    return omega, z, eta, delta
+
+
+def gibbs_step(X, y, beta, lam, nu, tau, xi, seed, step, *, tol=1e-6, stop_rule=STOP_RMS,
+               max_iter=10_000, draw="chol", **pcg_kw):
+    """One cycle of the Gibbs sampler of Sec. S1: tau, then lambda, then
+    omega, then beta (Prop. 2.1: by Cholesky, draw="chol", or by the oracle's
+    PCG, draw="cg").  Returns a dict with the new state and the beta draw's
+    iteration count."""
+    lam, nu, tau, xi = gibbs_scales(beta, lam, nu, tau, xi, seed, step)
+    omega, z, eta, delta = gibbs_omega(X, y, beta, seed, step)
+    k = 0
+    if draw == "chol":
+        beta = draw_beta_chol(X, omega, z, lam, tau, eta, delta)
+    else:
+        beta, k, _, st = draw_beta_cg(X, omega, z, lam, tau, eta, delta, tol=tol, stop_rule=stop_rule,
+                                      max_iter=max_iter, **pcg_kw)
+    return dict(beta=beta, lam=lam, nu=nu, tau=tau, xi=xi, omega=omega, z=z, eta=eta, delta=delta, iters=k)
 
 
 def dense_phi(X, omega, lam, tau):

@@ -647,3 +647,280 @@ void oracle_chol_solve(int64_t p, const double *l, const double *b, double *x)
         x[i] = e / l[i * p + i];
     }
 }
+
+/* ===========================================================================
+ * The rest of the Gibbs cycle of Sec. S1 (row f3): tau | beta, lambda;
+ * lambda | beta, tau; omega | beta ~ PolyaGamma(1, x_i^T beta); then the beta
+ * draw above.  Horseshoe prior: half-Cauchy local scales lambda_j and global
+ * scale tau (Sec. S1 names it beside the bridge), updated through the
+ * auxiliary variables of Makalic and Schmidt (2016): with nu_j, xi,
+ *   lambda_j^2 | nu_j ~ InvGamma(1/2, 1/nu_j),  nu_j ~ InvGamma(1/2, 1)
+ * (so lambda_j ~ C+(0, 1)), and likewise tau^2 with xi, the conditionals are
+ *   xi | tau          ~ InvGamma(1, 1 + 1/tau^2)
+ *   tau^2 | beta, lambda, xi ~ InvGamma((p + 1)/2, 1/xi + sum_j beta_j^2 / (2 lambda_j^2))
+ *   nu_j | lambda_j   ~ InvGamma(1, 1 + 1/lambda_j^2)
+ *   lambda_j^2 | beta_j, tau, nu_j ~ InvGamma(1, 1/nu_j + beta_j^2 / (2 tau^2)).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw 2011), a
+ * counter-based generator, keyed by a 64-bit seed; each quantity reads its own
+ * counter (index, stream, step, draw), so every element's numbers are fixed
+ * whatever order the elements are computed in.
+ * =========================================================================== */
+
+#define ORACLE_STREAM_XI 1u
+#define ORACLE_STREAM_TAU 2u
+#define ORACLE_STREAM_NU 3u
+#define ORACLE_STREAM_LAMBDA 4u
+#define ORACLE_STREAM_OMEGA 5u
+#define ORACLE_STREAM_ETA 6u
+#define ORACLE_STREAM_DELTA 7u
+
+/* One Philox4x32-10 block: ten rounds of the Philox S-box on the 4-word
+ * counter, the key bumped by the Weyl constants between rounds. */
+void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A stream of uniforms for one (index, stream, step): each block gives two
+ * doubles in (0, 1), ((w0 >> 5) 2^26 + (w1 >> 6) + 1/2) / 2^53 and the same
+ * from (w2, w3); the fourth counter word counts blocks. */
+typedef struct {
+    uint32_t key[2], ctr[3], draw;
+    double buf[2];
+    int have;
+} orng;
+
+static void orng_init(orng *g, uint64_t seed, uint32_t index, uint32_t stream, uint32_t step)
+{
+    g->key[0] = (uint32_t)seed;
+    g->key[1] = (uint32_t)(seed >> 32);
+    g->ctr[0] = index;
+    g->ctr[1] = stream;
+    g->ctr[2] = step;
+    g->draw = 0;
+    g->have = 0;
+}
+
+static double orng_u53(uint32_t a, uint32_t b)
+{
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) / 9007199254740992.0;
+}
+
+static double orng_uniform(orng *g)
+{
+    if (g->have == 0) {
+        const uint32_t c[4] = {g->ctr[0], g->ctr[1], g->ctr[2], g->draw};
+        uint32_t w[4];
+        oracle_philox(c, g->key, w);
+        g->draw += 1;
+        g->buf[0] = orng_u53(w[0], w[1]);
+        g->buf[1] = orng_u53(w[2], w[3]);
+        g->have = 2;
+    }
+    g->have -= 1;
+    return g->buf[1 - g->have];
+}
+
+/* Exponential(1) by inversion; standard normal by Box and Muller (the cosine
+ * branch only: two uniforms per normal). */
+static double orng_exp(orng *g) { return -log(orng_uniform(g)); }
+
+static double orng_normal(orng *g)
+{
+    const double u1 = orng_uniform(g), u2 = orng_uniform(g);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+/* Gamma(a, 1), a >= 1 (Marsaglia and Tsang 2000): d = a - 1/3, c = 1/sqrt(9d);
+ * repeat x ~ N(0,1), v = (1 + c x)^3 until v > 0 and log U < x^2/2 + d - d v + d log v. */
+static double orng_gamma(orng *g, double a)
+{
+    const double d = a - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+    for (int attempt = 0; attempt < 100000; ++attempt) {
+        const double x = orng_normal(g);
+        double v = 1.0 + c * x;
+        if (v <= 0.0) continue;
+        v = v * v * v;
+        const double u = orng_uniform(g);
+        if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+    }
+    return NAN;
+}
+
+/* Standard normal CDF. */
+static double ophi(double x) { return 0.5 * erfc(-x / 1.4142135623730951); }
+
+/* n-th coefficient of the alternating series of the J*(1, 0) density
+ * (Devroye's piecewise form, split at t). */
+static double pg_coef(int n, double x, double t)
+{
+    const double h = n + 0.5;
+    if (x > t) return 3.141592653589793 * h * exp(-h * h * 9.869604401089358 * x / 2.0);
+    return 3.141592653589793 * h * pow(2.0 / (3.141592653589793 * x), 1.5) * exp(-2.0 * h * h / x);
+}
+
+/* The J*(1, 0) density by its alternating series, sum_{n < terms} (-1)^n a_n(x),
+ * with the coefficients of the form chosen by t (x <= t: the small-x form,
+ * x > t: the large-x form).  Both forms represent the same density. */
+double oracle_pg_series(double x, double t, int terms)
+{
+    double s = 0.0;
+    for (int n = 0; n < terms; ++n)
+        s += (n & 1) ? -pg_coef(n, x, t) : pg_coef(n, x, t);
+    return s;
+}
+
+/* Inverse Gaussian IG(mu, 1) truncated to (0, t) (Polson, Scott and Windle 2013). */
+static double pg_trunc_ig(orng *g, double z, double t)
+{
+    const double mu = z > 0.0 ? 1.0 / z : INFINITY;
+    if (mu > t) {
+        for (int attempt = 0; attempt < 100000; ++attempt) {
+            double e1, e2;
+            do {
+                e1 = orng_exp(g);
+                e2 = orng_exp(g);
+            } while (e1 * e1 > 2.0 * e2 / t);
+            const double x = t / ((1.0 + t * e1) * (1.0 + t * e1));
+            const double alpha = exp(-0.5 * z * z * x);
+            if (orng_uniform(g) <= alpha) return x;
+        }
+        return NAN;
+    }
+    for (int attempt = 0; attempt < 100000; ++attempt) {
+        const double y0 = orng_normal(g);
+        const double y = y0 * y0;
+        double x = mu + 0.5 * mu * mu * y - 0.5 * mu * sqrt(4.0 * mu * y + (mu * y) * (mu * y));
+        if (orng_uniform(g) > mu / (mu + x)) x = mu * mu / x;
+        if (x <= t) return x;
+    }
+    return NAN;
+}
+
+/*
+ * One draw of PolyaGamma(1, c) (Polson, Scott and Windle 2013): X ~ J*(1, z),
+ * z = |c|/2, by Devroye's alternating-series method with the proposal mixing
+ * a truncated exponential on (t, inf) and a truncated inverse Gaussian on
+ * (0, t), t = 0.64; omega = X / 4.
+ */
+double oracle_pg1_draw(double c, orng *g)
+{
+    const double t = 0.64, z = 0.5 * fabs(c);
+    const double K = 9.869604401089358 / 8.0 + 0.5 * z * z;
+    const double p = 3.141592653589793 / (2.0 * K) * exp(-K * t);
+    double q;
+    if (z > 0.0) {
+        const double mu = 1.0 / z, rt = sqrt(1.0 / t);
+        q = 2.0 * exp(-z) * (ophi(rt * (t / mu - 1.0)) + exp(2.0 / mu) * ophi(-rt * (t / mu + 1.0)));
+    } else {
+        q = 4.0 * ophi(-sqrt(1.0 / t));
+    }
+    const double r = p / (p + q);
+    /* a proposal is accepted with probability above 0.99 and the series decides
+     * within a few terms: the caps only end a sampler that is broken (NaN) */
+    for (int attempt = 0; attempt < 100000; ++attempt) {
+        double x;
+        if (orng_uniform(g) < r) x = t + orng_exp(g) / K;
+        else x = pg_trunc_ig(g, z, t);
+        double s = pg_coef(0, x, t);
+        const double y = orng_uniform(g) * s;
+        for (int n = 1; n < 1000; ++n) {
+            if (n & 1) {
+                s -= pg_coef(n, x, t);
+                if (y <= s) return 0.25 * x;
+            } else {
+                s += pg_coef(n, x, t);
+                if (y > s) break;
+            }
+        }
+    }
+    return NAN;
+}
+
+/* out[k] = PolyaGamma(1, c[k]) with index k's numbers of (seed, stream, step). */
+void oracle_pg1(int64_t m, const double *c, uint64_t seed, uint32_t stream, uint32_t step, double *out)
+{
+    for (int64_t k = 0; k < m; ++k) {
+        orng g;
+        orng_init(&g, seed, (uint32_t)k, stream, step);
+        out[k] = oracle_pg1_draw(c[k], &g);
+    }
+}
+
+/* Uniforms, exponentials, normals and Gamma(a) draws of one counter (pins). */
+void oracle_rng_draws(int kind, int64_t m, uint64_t seed, uint32_t index, uint32_t stream,
+                      uint32_t step, double a, double *out)
+{
+    orng g;
+    orng_init(&g, seed, index, stream, step);
+    for (int64_t k = 0; k < m; ++k)
+        out[k] = kind == 0 ? orng_uniform(&g) : kind == 1 ? orng_exp(&g)
+               : kind == 2 ? orng_normal(&g) : orng_gamma(&g, a);
+}
+
+/*
+ * The scale updates of one Gibbs cycle (steps 1-2 of Sec. S1):
+ *   xi ~ IG(1, 1 + 1/tau^2), tau^2 ~ IG((p+1)/2, 1/xi + sum_j beta_j^2/(2 lambda_j^2)),
+ *   nu_j ~ IG(1, 1 + 1/lambda_j^2), lambda_j^2 ~ IG(1, 1/nu_j + beta_j^2/(2 tau^2)),
+ * with IG(a, b) = b / Gamma(a, 1) (Gamma(1, 1) = Exponential(1)).  tau, xi:
+ * in/out scalars; lambda, nu: in/out p-vectors.
+ */
+void oracle_gibbs_scales(int64_t p, const double *beta, double *lam, double *nu, double *tau,
+                         double *xi, uint64_t seed, uint32_t step)
+{
+    orng g;
+    orng_init(&g, seed, 0u, ORACLE_STREAM_XI, step);
+    *xi = (1.0 + 1.0 / ((*tau) * (*tau))) / orng_exp(&g);
+    double ssq = 0.0;
+    for (int64_t j = 0; j < p; ++j)
+        ssq += beta[j] * beta[j] / (2.0 * lam[j] * lam[j]);
+    orng_init(&g, seed, 0u, ORACLE_STREAM_TAU, step);
+    *tau = sqrt((1.0 / *xi + ssq) / orng_gamma(&g, 0.5 * (double)(p + 1)));
+    for (int64_t j = 0; j < p; ++j) {
+        orng_init(&g, seed, (uint32_t)j, ORACLE_STREAM_NU, step);
+        nu[j] = (1.0 + 1.0 / (lam[j] * lam[j])) / orng_exp(&g);
+        orng_init(&g, seed, (uint32_t)j, ORACLE_STREAM_LAMBDA, step);
+        lam[j] = sqrt((1.0 / nu[j] + beta[j] * beta[j] / (2.0 * (*tau) * (*tau))) / orng_exp(&g));
+    }
+}
+
+/*
+ * Step 3 of Sec. S1 and the Gaussian vectors of Prop. 2.1 for step 4:
+ *   psi = X beta; omega_i ~ PolyaGamma(1, psi_i); z_i = (y_i - 1/2) / omega_i (Eq. 1.1);
+ *   eta ~ N(0, I_n), delta ~ N(0, I_p).
+ */
+void oracle_gibbs_omega(int64_t n, int64_t p, const int64_t *row_ptr, const int32_t *col_idx,
+                        const double *y, const double *beta, uint64_t seed, uint32_t step,
+                        double *omega, double *z, double *eta, double *delta)
+{
+    double *psi = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    oracle_x_mul(n, row_ptr, col_idx, beta, psi);
+    oracle_pg1(n, psi, seed, ORACLE_STREAM_OMEGA, step, omega);
+    for (int64_t i = 0; i < n; ++i) {
+        z[i] = (y[i] - 0.5) / omega[i];
+        orng g;
+        orng_init(&g, seed, (uint32_t)i, ORACLE_STREAM_ETA, step);
+        eta[i] = orng_normal(&g);
+    }
+    for (int64_t j = 0; j < p; ++j) {
+        orng g;
+        orng_init(&g, seed, (uint32_t)j, ORACLE_STREAM_DELTA, step);
+        delta[j] = orng_normal(&g);
+    }
+    free(psi);
+}

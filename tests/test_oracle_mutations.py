@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from tests import test_oracle_gibbs as gibbs
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -44,6 +45,14 @@ MUTANTS = {
     "lsqr_theta_uses_c": ("const double theta = sn * alf;", "const double theta = c * alf;"),
     "lsqr_bottom_block_dropped": ("u[n + j] = v[j] - alf * u[n + j];", "u[n + j] = - alf * u[n + j];"),
     "lsqr_eta_dropped": ("u[i] = sqrt(omega[i]) * z[i] + eta[i];", "u[i] = sqrt(omega[i]) * z[i];"),
+    "philox_wrong_weyl": ("k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;"),
+    "pg_coef_exponent": ("exp(-h * h * 9.869604401089358 * x / 2.0)", "exp(-h * h * 9.869604401089358 * x)"),
+    "pg_mixture_weight": ("const double r = p / (p + q);", "const double r = q / (p + q);"),
+    "pg_half_tilt": ("const double t = 0.64, z = 0.5 * fabs(c);", "const double t = 0.64, z = fabs(c);"),
+    "lambda_scale_tau_not_squared": ("beta[j] * beta[j] / (2.0 * (*tau) * (*tau))) / orng_exp(&g));",
+                                     "beta[j] * beta[j] / (2.0 * (*tau))) / orng_exp(&g));"),
+    "tau_shape_drops_one": ("orng_gamma(&g, 0.5 * (double)(p + 1))", "orng_gamma(&g, 0.5 * (double)(p + 3))"),
+    "augmented_response_times_omega": ("z[i] = (y[i] - 0.5) / omega[i];", "z[i] = (y[i] - 0.5) * omega[i];"),
 }
 
 # the pins that run against each mutant (the slow statistical ones are left out:
@@ -71,6 +80,12 @@ PIN_TESTS = [
     pins.test_lsqr_solves_the_normal_equations,
     pins.test_lsqr_iterates_equal_pcg_iterates,
     pins.test_lsqr_residual_estimate_is_eq_s2,
+    gibbs.test_philox_known_answers,
+    gibbs.test_polya_gamma_series_forms_agree,
+    lambda: gibbs.test_polya_gamma_moments(0.4),
+    lambda: gibbs.test_polya_gamma_moments(8.0),
+    gibbs.test_scale_updates_draw_their_conditionals,
+    gibbs.test_gibbs_step_composes_the_cycle,
 ]
 
 
