@@ -470,6 +470,7 @@ def run_ours(args):
     forms = None
     if rank == 0 and not args.no_forms:
         forms = other_forms(pb, dev, stream)
+        forms.update(single_forms(pb, dev, stream, P, X, ins))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -599,6 +600,60 @@ def host_cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+def single_forms(pb, dev, stream, P, X, ins):
+    """Chain 0 of the bench workload as single-RHS draws on the same GPU and
+    stop rule: the Jacobi against the prior preconditioner (Sec. 2.4, Sec.
+    3), a warm start from the previous draw against a cold start (Sec.
+    S4.1), and LSQR on the least-squares form (Sec. S7.1) against CG, both
+    in float64."""
+    import torch
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    ch = lambda k: ins[k][0].contiguous()
+    args = (ch("omega"), ch("z"), ch("lam"), float(P.tau[0]), ch("eta"), ch("delta"))
+
+    def timed(fn, reps=2):
+        fn()                                   # graph capture, plans
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize(dev)
+        return r, reps / (time.perf_counter() - t0)
+
+    out = {"workload": "chain 0 of the bench workload (n=500000, p=50000), single-RHS draws"}
+    pre = {}
+    for name in ("prior", "jacobi"):
+        c = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, preconditioner=name)
+        r, rate = timed(lambda: pb.pcg_draw_beta(c, X, *args, tol=TOL, max_iter=20_000))
+        pre[name] = {"iters": r.iters, "draws_per_s": rate, "status": r.status}
+    out["preconditioner"] = pre
+    # warm start from the previous draw (the same omega, lambda, tau; fresh eta, delta)
+    rng = np.random.default_rng(99)
+    eta2, delta2 = T(rng.standard_normal(P.X.n)), T(rng.standard_normal(P.X.p))
+    cold = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream)
+    first = pb.pcg_draw_beta(cold, X, *args, tol=TOL, max_iter=20_000).beta.clone()
+    warm = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, warm_start=True)
+    a2 = (args[0], args[1], args[2], args[3], eta2, delta2)
+    buf = torch.empty_like(first)
+    rc, rate_c = timed(lambda: pb.pcg_draw_beta(cold, X, *a2, tol=TOL, max_iter=20_000))
+
+    def warm_draw():
+        buf.copy_(first)
+        return pb.pcg_draw_beta(warm, X, *a2, tol=TOL, max_iter=20_000, out=buf)
+
+    rw, rate_w = timed(warm_draw)
+    out["warm_start"] = {"cold_iters": rc.iters, "warm_iters": rw.iters, "cold_draws_per_s": rate_c,
+                         "warm_draws_per_s": rate_w,
+                         "beta_0": "the previous draw of the same conditional (fresh eta, delta)"}
+    f64 = pb.Context(precision="fp64", stream=stream)
+    rl, rate_l = timed(lambda: pb.pcg_draw_beta_lsqr(f64, X, *args, tol=TOL, max_iter=20_000), reps=1)
+    rp, rate_p = timed(lambda: pb.pcg_draw_beta(f64, X, *args, tol=TOL, max_iter=20_000), reps=1)
+    out["lsqr"] = {"lsqr_iters": rl.iters, "lsqr_draws_per_s": rate_l, "cg_iters": rp.iters,
+                   "cg_draws_per_s": rate_p, "precision": "fp64 (LSQR: untiled float64 gathers; "
+                   "CG: the tiled float64 products)"}
+    return out
 
 
 def cpu_baseline(P, gpu_iters):
