@@ -506,31 +506,34 @@ def other_forms(pb, dev, stream):
     probs = inputs.config4()
     dp = [dict(X=pb.DeviceDesign.from_host(P.X, dev), omega=T(P.omega), z=T(P.z), lam=T(P.lam),
                tau=float(P.tau), eta=T(P.eta), delta=T(P.delta)) for P in probs]
-    ctx = pb.Context(precision="fp32_refined", stream=stream)
-    pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)          # tunes and builds the graph
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    res = pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)
-    torch.cuda.synchronize(dev)
-    t_uneven = time.perf_counter() - t0
-    sctx = pb.Context(precision="fp32_refined", stream=stream)
-    for d in dp[:2]:
-        pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"], tol=TOL)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    s_iters = []
-    for d in dp:
-        r = pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"],
-                             tol=TOL, max_iter=20_000)
-        s_iters.append(r.iters)
-    torch.cuda.synchronize(dev)
-    t_single = time.perf_counter() - t0
+    def uneven_vs_single(prec):
+        ctx = pb.Context(precision=prec, stream=stream)
+        pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)      # tunes and builds the graph
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = pb.pcg_draw_beta_uneven(ctx, dp, tol=TOL, max_iter=20_000)
+        torch.cuda.synchronize(dev)
+        t_uneven = time.perf_counter() - t0
+        sctx = pb.Context(precision=prec, stream=stream)
+        for d in dp[:2]:
+            pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"], tol=TOL)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s_iters = []
+        for d in dp:
+            r = pb.pcg_draw_beta(sctx, d["X"], d["omega"], d["z"], d["lam"], d["tau"], d["eta"], d["delta"],
+                                 tol=TOL, max_iter=20_000)
+            s_iters.append(r.iters)
+        torch.cuda.synchronize(dev)
+        t_single = time.perf_counter() - t0
+        return {"persistent_kernel_draws_per_s": len(dp) / t_uneven,
+                "single_rhs_draws_per_s": len(dp) / t_single,
+                "iters_sum_uneven": int(sum(r.iters for r in res)), "iters_sum_single": int(sum(s_iters)),
+                "status_ok": all(r.status == 0 for r in res)}
+
     out["uneven"] = {"workload": "64 problems, n~logU[5e3,2e5], p~logU[1e3,3e4], log10 r~U(-4,-1.5), tau=0.01",
                      "nnz_total": int(sum(P.X.nnz for P in probs)),
-                     "persistent_kernel_draws_per_s": len(dp) / t_uneven,
-                     "single_rhs_draws_per_s": len(dp) / t_single,
-                     "iters_sum_uneven": int(sum(r.iters for r in res)), "iters_sum_single": int(sum(s_iters)),
-                     "status_ok": all(r.status == 0 for r in res)}
+                     "fp32_refined": uneven_vs_single("fp32_refined"), "fp64": uneven_vs_single("fp64")}
     del dp
     # adjoint: gradient of c^T beta on n=2e5, p=2e4
     P = inputs.config5()
@@ -653,6 +656,31 @@ def single_forms(pb, dev, stream, P, X, ins):
     out["lsqr"] = {"lsqr_iters": rl.iters, "lsqr_draws_per_s": rate_l, "cg_iters": rp.iters,
                    "cg_draws_per_s": rate_p, "precision": "fp64 (LSQR: untiled float64 gathers; "
                    "CG: the tiled float64 products)"}
+    # whole Gibbs cycles of Sec. S1 (horseshoe; tau, lambda, omega updates + the draw)
+    y = T(P.y[0])
+    gctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream)
+    beta_start = pb.pcg_draw_beta(gctx, X, *args, tol=TOL, max_iter=20_000).beta.clone()
+    gst = pb.GibbsState(omega=ch("omega").clone(), lam=ch("lam").clone(),
+                        nu=torch.ones(P.X.p, dtype=torch.float64, device=dev),
+                        beta=beta_start, tau=float(P.tau[0]), xi=1.0)
+    pb.pcg_gibbs_step(gctx, X, y, gst, seed=2018, step=0, tol=TOL, max_iter=20_000)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    g_iters = []
+    for k in range(1, 4):
+        g_iters.append(pb.pcg_gibbs_step(gctx, X, y, gst, seed=2018, step=k, tol=TOL, max_iter=20_000).iters)
+    torch.cuda.synchronize(dev)
+    rate_g = 3 / (time.perf_counter() - t0)
+    pctx = pb.Context(precision=PRECISION, reliable_k=RELIABLE_K, stream=stream, profile=True)
+    pb.pcg_gibbs_step(pctx, X, y, gst, seed=2018, step=4, tol=TOL, max_iter=20_000)
+    tab = pb.profile_table(pctx)
+    upd_ms = sum(v[0] for k, v in tab.items() if k.startswith("g_"))
+    out["gibbs"] = {"steps_per_s": rate_g, "draw_iters": g_iters,
+                    "updates_ms": upd_ms, "tau": gst.tau,
+                    "note": "cycles 1-3 from the workload's omega, lambda, tau and a draw of beta given them "
+                            "(y carries no signal, so the chain moves towards smaller tau and shorter "
+                            "draws); updates_ms: tau, lambda, psi = X beta, omega, eta, delta kernels "
+                            "of one cycle"}
     return out
 
 

@@ -229,6 +229,31 @@ pcg_status pcg_draw_beta_lsqr(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc 
                               double *beta, int *iters, double *resid);
 
 /*
+ * One cycle of the Gibbs sampler of Sec. S1 for sparse logistic regression with
+ * Polya-Gamma augmentation and the horseshoe prior (half-Cauchy local scales
+ * lambda_j and global scale tau, Sec. S1), in the order the paper gives:
+ *   1. tau | beta, lambda   2. lambda | beta, tau   3. omega_i | beta ~ PolyaGamma(1, x_i^T beta)
+ *   4. beta | omega, tau, lambda, y by pcg_draw_beta with z_i = (y_i - 1/2) / omega_i (Eq. 1.1)
+ *      and fresh eta ~ N(0, I_n), delta ~ N(0, I_p).
+ * Steps 1-2 use the auxiliary variables of Makalic and Schmidt (2016): xi ~
+ * IG(1, 1 + 1/tau^2), tau^2 ~ IG((p+1)/2, 1/xi + sum beta_j^2 / (2 lambda_j^2)),
+ * nu_j ~ IG(1, 1 + 1/lambda_j^2), lambda_j^2 ~ IG(1, 1/nu_j + beta_j^2 / (2 tau^2)).
+ * Random numbers: Philox4x32-10 keyed by `seed`, one counter per (element,
+ * quantity, step): the cycle is a deterministic function of (state, seed, step).
+ * y: device, n values in {0, 1}.  In/out state: omega (device, n; out only),
+ * lambda, nu, beta (device, p), *tau and *xi (host).  beta holds beta* on entry
+ * (the previous draw, also beta_0 under warm_start) and the new draw on return.
+ * The draw uses the context's precision, stop rule and preconditioner; tol,
+ * max_iter, iters and resid as pcg_draw_beta.  PCG_BADARG while unshrunk
+ * coefficients are set; PCG_NONFINITE if an update leaves tau or xi
+ * non-finite.
+ */
+pcg_status pcg_gibbs_step(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc, const double *y,
+                          uint64_t seed, uint32_t step, double *omega, double *lambda, double *nu,
+                          double *tau, double *xi, double *beta, double tol, int max_iter, int *iters,
+                          double *resid);
+
+/*
  * CG solve of Phi x = rhs (Eq. 2.4) for a given right-hand side (no Eq. 2.3
  * step); same outputs as pcg_draw_beta.  Used by the adjoint, whose second
  * solve Phi g = c shares Phi and the preconditioner.

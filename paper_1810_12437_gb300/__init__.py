@@ -12,4 +12,4 @@ from ._native import (  # noqa: F401
     pcg_draw_beta, pcg_draw_beta_batched, pcg_draw_beta_uneven, pcg_last_error, pcg_phi_mul,
     pcg_last_kernel_launches, pcg_profile_count, pcg_profile_entry, pcg_profile_reset,
     pcg_solve, profile_table, pcg_phi_mul_noalloc, NOALLOC_MAX_N, pcg_set_unshrunk,
-    pcg_tiled_plan_applies, pcg_draw_beta_lsqr)
+    pcg_tiled_plan_applies, pcg_draw_beta_lsqr, pcg_gibbs_step, GibbsState)

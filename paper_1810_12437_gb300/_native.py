@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH):
             "pcg_phi_mul_noalloc": ([pCsr, pCsc, P, P, D, P, P, P], I),
             "pcg_tiled_plan_applies": ([I64, I64, I64, I, I, pI, pI], I),
             "pcg_draw_beta_lsqr": ([P, pCsr, pCsc, P, P, P, D, P, P, D, I, P, pI, pD], I),
+            "pcg_gibbs_step": ([P, pCsr, pCsc, P, ctypes.c_uint64, ctypes.c_uint32, P, P, P, pD, pD, P, D, I,
+                                pI, pD], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -113,7 +115,8 @@ def exported_symbols() -> Sequence[str]:
             "pcg_check_design", "pcg_build_rhs", "pcg_phi_mul", "pcg_draw_beta", "pcg_solve",
             "pcg_draw_beta_batched", "pcg_draw_beta_uneven", "pcg_adjoint", "pcg_profile_count",
             "pcg_profile_entry", "pcg_profile_reset", "pcg_last_kernel_launches",
-            "pcg_phi_mul_noalloc", "pcg_set_unshrunk", "pcg_tiled_plan_applies", "pcg_draw_beta_lsqr"]
+            "pcg_phi_mul_noalloc", "pcg_set_unshrunk", "pcg_tiled_plan_applies", "pcg_draw_beta_lsqr",
+            "pcg_gibbs_step"]
 
 
 # ---------------------------------------------------------------------------
@@ -358,6 +361,40 @@ def pcg_draw_beta_lsqr(ctx, X, omega, z, lam, tau, eta, delta, tol=1e-6, max_ite
                                                    _ptr(delta), float(tol), int(max_iter), _ptr(out),
                                                    ctypes.byref(it), ctypes.byref(rs)))
     return DrawResult(out, it.value, rs.value, st)
+
+
+@dataclasses.dataclass
+class GibbsState:
+    """State of the Gibbs sampler of Sec. S1 (horseshoe prior): device
+    vectors omega (n), lam, nu, beta (p) and host scalars tau, xi."""
+    omega: torch.Tensor
+    lam: torch.Tensor
+    nu: torch.Tensor
+    beta: torch.Tensor
+    tau: float
+    xi: float
+
+
+def pcg_gibbs_step(ctx, X, y, state: GibbsState, seed: int, step: int, tol=1e-6, max_iter=10_000):
+    """One cycle tau -> lambda -> omega -> beta of Sec. S1, in place on
+    `state`; returns the beta draw's DrawResult (beta is state.beta)."""
+    f = torch.float64
+    dev = X.device
+    _dev(y, f, X.n, "y", dev)
+    _dev(state.omega, f, X.n, "omega", dev)
+    for name, t in (("lambda", state.lam), ("nu", state.nu), ("beta", state.beta)):
+        _dev(t, f, X.p, name, dev)
+    csr, csc = X.csr(), X.csc()
+    it, rs = ctypes.c_int(0), ctypes.c_double(0.0)
+    tau, xi = ctypes.c_double(state.tau), ctypes.c_double(state.xi)
+    with torch.cuda.device(ctx.device):
+        st = ctx.check(ctx._lib.pcg_gibbs_step(ctx.handle, ctypes.byref(csr), ctypes.byref(csc), _ptr(y),
+                                               int(seed) & (2 ** 64 - 1), int(step) & 0xffffffff,
+                                               _ptr(state.omega), _ptr(state.lam), _ptr(state.nu),
+                                               ctypes.byref(tau), ctypes.byref(xi), _ptr(state.beta),
+                                               float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rs)))
+    state.tau, state.xi = tau.value, xi.value
+    return DrawResult(state.beta, it.value, rs.value, st)
 
 
 def pcg_solve(ctx, X, omega, lam, tau, rhs, tol=1e-6, max_iter=10_000, out=None):

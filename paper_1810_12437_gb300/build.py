@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_pcg_beta.so")
 SOURCES = ["capi.cu", "single.cu", "batched.cu", "uneven.cu", "adjoint.cu", "noalloc.cu", "tiled.cu",
-           "lsqr.cu"]
+           "lsqr.cu", "gibbs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-diag-suppress", "177", f"-I{os.path.join(ROOT, 'include')}"]

@@ -438,6 +438,31 @@ pcg_status pcg_draw_beta_lsqr(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc
     return run_lsqr(ctx, Xr, Xc, omega, z, lambda, tau, eta, delta, tol, max_iter, beta, iters, resid);
 }
 
+pcg_status pcg_gibbs_step(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *y, uint64_t seed,
+                          uint32_t step, double *omega, double *lambda, double *nu, double *tau, double *xi,
+                          double *beta, double tol, int max_iter, int *iters, double *resid) {
+    if (!ctx) return PCG_BADARG;
+    ctx->last_launches = 0;
+    if (!iters || !resid || !tau || !xi) return set_error(ctx, PCG_BADARG, "NULL host argument");
+    *iters = 0;
+    *resid = 0.0;
+    pcg_status st = check_shapes(ctx, Xr, Xc);
+    if (st != PCG_OK) return st;
+    if (bad_scalar(*tau) || bad_scalar(*xi)) return set_error(ctx, PCG_BADARG, "tau and xi must be positive and finite");
+    if (!(tol >= 0.0) || max_iter < 0) return set_error(ctx, PCG_BADARG, "tol >= 0 and max_iter >= 0 required");
+    if (ctx->unshrunk_q1 > 0)
+        return set_error(ctx, PCG_BADARG, "the Gibbs step puts every coefficient under the horseshoe prior");
+    if (Xr->p == 0) return PCG_OK;
+    if ((Xr->n > 0 && (!y || !omega)) || !lambda || !nu || !beta) return set_error(ctx, PCG_BADARG, "NULL vector");
+    const double *z = nullptr, *eta = nullptr, *delta = nullptr;
+    st = run_gibbs_updates(ctx, Xr, y, seed, step, omega, lambda, nu, tau, xi, beta, &z, &eta, &delta);
+    if (st != PCG_OK) return st;
+    const int64_t upd = ctx->last_launches;
+    st = pcg_draw_beta(ctx, Xr, Xc, omega, z, lambda, *tau, eta, delta, tol, max_iter, beta, iters, resid);
+    ctx->last_launches += upd;
+    return st;
+}
+
 pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const double *omega,
                      const double *lambda, double tau, const double *rhs, double tol, int max_iter,
                      double *x, int *iters, double *resid) {

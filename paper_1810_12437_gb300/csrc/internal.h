@@ -205,6 +205,13 @@ pcg_status run_lsqr(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, const do
                     const double *delta, double tol, int max_iter, double *beta, int *iters,
                     double *resid);
 
+// the rest of the Gibbs cycle (gibbs.cu): tau, lambda, omega and the Gaussian
+// vectors of Prop. 2.1 into context workspace (z, eta, delta)
+pcg_status run_gibbs_updates(pcg_ctx *ctx, const pcg_csr *Xr, const double *y, uint64_t seed, uint32_t step,
+                             double *omega, double *lambda, double *nu, double *tau, double *xi,
+                             const double *beta, const double **z_out, const double **eta_out,
+                             const double **delta_out);
+
 // uneven batch (uneven.cu)
 pcg_status run_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol, int max_iter,
                       int *iters, double *resid, int *status);
