@@ -233,3 +233,34 @@ def test_batched_full_size_pair_products_match_oracle_samples(pb, prec):
         b = O.build_b(P.X, om, z, lam, tau, eta, delta)
         rt = tau * lam * (b - O.phi_mul(P.X, om, lam, tau, beta[r]))
         assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6, r
+
+
+@pytest.mark.parametrize("prec", ["df32", "fx64", "fp32"])
+def test_batched_single_pass_update(pb, small3, prec, monkeypatch):
+    """The optional single-pass CG update (PCG_BETA_FUSED_UPDATE=1: the
+    finalize forms gamma from r.M^-1 v and v.M^-1 v, one kernel then updates
+    beta, r, s and computes rho') against the default two-pass update.  Both
+    draws match the oracle's within 1e-5 (1e-3 in float32) and the fused
+    form runs one kernel fewer per iteration; only the default keeps the
+    iteration window (the recurrence for rho' costs iterations on these
+    systems, which is why it is not the default)."""
+    P = small3
+    X = __import__("paper_1810_12437_gb300").DeviceDesign.from_host(P.X, dev())
+    runs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PCG_BETA_FUSED_UPDATE", flag)
+        ctx = pb.Context(precision=prec)
+        res = pb.pcg_draw_beta_batched(ctx, X, **batched_args(P), tol=1e-6, max_iter=5000)
+        runs[flag] = (res, pb.pcg_last_kernel_launches(ctx))
+    # graph launches: 3 set-up kernels plus a fixed count per loop trip
+    per_trip = {f: (launches - 3) / max(res.iters) for f, (res, launches) in runs.items()}
+    assert per_trip["0"] - per_trip["1"] == 1, per_trip
+    bound = 1e-5 if prec != "fp32" else 1e-3
+    for r in (0, 2, 4, 9, 15):
+        om, z, lam, tau, eta, delta = chain(P, r)
+        ref = O.draw_beta_cg(P.X, om, z, lam, tau, eta, delta, tol=1e-6)[0]
+        w = problem_window(prec, P, r)
+        for flag, (res, _) in runs.items():
+            assert res.status[r] == pb.PCG_OK, (flag, r)
+            assert rel(res.beta.cpu().numpy()[r], ref) < bound, (flag, r)
+        assert w.holds(runs["0"][0].iters[r]), (r, runs["0"][0].iters[r], str(w))
