@@ -234,6 +234,22 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def smem_wavefronts_for(kernel, groups_per_launch):
+    """ncu shared-memory wavefronts (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum)
+    per launch, from profiles/traffic.json under the same source guard as the
+    traffic; None when absent or stale."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_sha") == kernel_source_sha() and "smem_wavefronts_per_group" in e:
+            return e["smem_wavefronts_per_group"] * groups_per_launch
+    except Exception:
+        pass
+    return None
+
+
 def traffic_for(kernel, groups_per_launch):
     """ncu DRAM bytes (read + write) per launch, from profiles/traffic.json,
     if they were taken on the current kernel source: the file holds the bytes
@@ -284,7 +300,7 @@ def survey_bytes(kernel, n, p, nnz, L):
     return None
 
 
-def roofline(table, acct, n, p, nnz, RG, peak, peak_kind):
+def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
     """Roofline entry of the dominant kernel and the per-kernel table.
     `achieved` uses the scope table's algorithmic bytes (survey_bytes) summed
     over the launches that did work, divided by the kernel's total CUDA-event
@@ -331,9 +347,18 @@ def roofline(table, acct, n, p, nnz, RG, peak, peak_kind):
     achieved = ab / work_launches / avg_s / 1e9 if ab else None
     impl_achieved = ib / work_launches / avg_s / 1e9 if ib else None
     groups_per_launch = (gu / work_launches) if (gu and kname.startswith(("bt_cs", "bt_u"))) else 1.0
+    wf = smem_wavefronts_for(kname, groups_per_launch)
+    smem = None
+    if wf:
+        # one shared-memory wavefront per clock per SM (152 SMs) at the sampled SM clock
+        peak_wf = 152 * (sm_mhz or 2070.0) * 1e6
+        smem = {"wavefronts_per_launch": wf, "achieved_per_s": wf / avg_s, "peak_per_s": peak_wf,
+                "frac": wf / avg_s / peak_wf,
+                "note": "ncu shared-memory wavefronts per group (profiles/traffic.json) x groups per launch, "
+                        "over the launch time; peak 1 wavefront/clock/SM"}
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_for(kname, groups_per_launch),
+            "traffic": traffic_for(kname, groups_per_launch), "shared_memory": smem,
             "peak_source": f"hbm_gbs of {peak_kind}",
             "bytes": "scope-table algorithmic bytes: int32 indices once per launch for all live "
                      "chains, vectors once per chain (survey_bytes)",
@@ -465,7 +490,7 @@ def run_ours(args):
     RG = tuned_group_width(tune_file)
     acct = product_accounting(list(pres.iters), RG, tail=any(k.startswith("bt1_") for k in table))
     peak, peak_kind = peaks()
-    roof = roofline(table, acct, P.X.n, P.X.p, P.X.nnz, RG, peak, peak_kind)
+    roof = roofline(table, acct, P.X.n, P.X.p, P.X.nnz, RG, peak, peak_kind, clk.get("sm_mhz"))
 
     forms = None
     if rank == 0 and not args.no_forms:
@@ -496,8 +521,9 @@ def run_ours(args):
 
 
 def other_forms(pb, dev, stream):
-    """The uneven batch and the adjoint, each against plain single-RHS PCG on
-    the same GPU, same precision (fp32 refined) and stop rule (RMS 1e-6)."""
+    """The uneven batch (float32 refined, float64 and double-float products)
+    and the adjoint (float32 refined), each against plain single-RHS PCG on the
+    same GPU, precision and stop rule (RMS 1e-6)."""
     import torch
     from paper_1810_12437_gb300 import inputs
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
@@ -533,7 +559,8 @@ def other_forms(pb, dev, stream):
 
     out["uneven"] = {"workload": "64 problems, n~logU[5e3,2e5], p~logU[1e3,3e4], log10 r~U(-4,-1.5), tau=0.01",
                      "nnz_total": int(sum(P.X.nnz for P in probs)),
-                     "fp32_refined": uneven_vs_single("fp32_refined"), "fp64": uneven_vs_single("fp64")}
+                     "fp32_refined": uneven_vs_single("fp32_refined"), "fp64": uneven_vs_single("fp64"),
+                     "df32": uneven_vs_single("df32")}
     del dp
     # adjoint: gradient of c^T beta on n=2e5, p=2e4
     P = inputs.config5()

@@ -293,9 +293,10 @@ typedef struct pcg_problem {
  * from a device queue; each problem advances its own CG with per-problem
  * barriers whose waits are bounded (PCG_TIMEOUT if one gives up).
  * probs: host array of nprob descriptors.  iters, resid, status: host, nprob.
- * Its products are float64 (PCG_PREC_FP64) or float32; PCG_PREC_DF32 and
- * PCG_PREC_FX64 run as PCG_PREC_FP32_REFINED (float32 products, float64
- * recomputation of r).
+ * Its products are float64 (PCG_PREC_FP64), double-float (PCG_PREC_DF32, and
+ * PCG_PREC_FX64, which runs as double-float here: float pairs gathered from L2
+ * and summed with TwoSum), or float32 (PCG_PREC_FP32, and PCG_PREC_FP32_REFINED
+ * with the float64 recomputation of r).
  */
 pcg_status pcg_draw_beta_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol,
                                 int max_iter, int *iters, double *resid, int *status);

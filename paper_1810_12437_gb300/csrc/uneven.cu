@@ -18,19 +18,24 @@
 // waits for another: an idle CTA backs off and gives up, setting a timeout
 // flag, if no tile anywhere completes for `idle_limit_ns`.
 //
-// Vectors written inside the kernel are read through L2 (ld.global.cg), never
-// through the non-coherent read-only path, because they change between phases.
+// Products: float64 (s64, u64, omega gathered), float32 (float copies) or
+// double-float (float-pair copies summed with TwoSum, about 48 bits; the
+// fixed-point mode runs as double-float here).  Vectors written inside the
+// kernel are read through L2 (ld.global.cg), never through the non-coherent
+// read-only path, because they change between phases.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 
 #include <algorithm>
 #include <fstream>
+#include <type_traits>
 #include <sstream>
 #include <string>
 #include <vector>
 
 #include "device_common.cuh"
+#include "df.cuh"
 #include "internal.h"
 
 namespace pcg {
@@ -52,6 +57,7 @@ struct UProb {
     int nt_row, nt_col, nt_vec;
     int rows_per_tile, cols_per_tile, vec_per_tile;
     int g_row, g_col;   // lanes per row / column (power of two <= 32)
+    int df;             // double-float products: s32, u32, om32 hold float pairs
 };
 
 struct __align__(128) UState {
@@ -98,6 +104,58 @@ __device__ __forceinline__ T gsum(T v, int g) {
     return v;
 }
 
+// A double-float value (a float pair summed with TwoSum, about 48 bits):
+// the gathered type of the double-float products of the persistent kernel.
+struct DFv {
+    float2 v;
+    __device__ __forceinline__ DFv() : v(make_float2(0.f, 0.f)) {}
+    __device__ __forceinline__ explicit DFv(int) : v(make_float2(0.f, 0.f)) {}
+    __device__ __forceinline__ explicit DFv(float2 x) : v(x) {}
+    __device__ __forceinline__ DFv operator+(const DFv &o) const { return DFv(df_add(v, o.v)); }
+    __device__ __forceinline__ DFv &operator+=(const DFv &o) { v = df_add(v, o.v); return *this; }
+    __device__ __forceinline__ DFv operator*(const DFv &o) const { return DFv(df_mul(v, o.v)); }
+    __device__ __forceinline__ explicit operator double() const { return df_to_double(v); }
+};
+
+template <>
+__device__ __forceinline__ DFv ldc<DFv>(const DFv *p) {
+    return DFv(__ldcg(reinterpret_cast<const float2 *>(p)));
+}
+
+template <>
+__device__ __forceinline__ DFv gsum<DFv>(DFv x, int g) {
+    for (int o = g >> 1; o > 0; o >>= 1) {
+        const float2 y = make_float2(__shfl_xor_sync(kFull, x.v.x, o), __shfl_xor_sync(kFull, x.v.y, o));
+        x += DFv(y);
+    }
+    return x;
+}
+
+// Where each product type reads and writes its vectors: float32 copies,
+// float64 originals, or float-pair copies (the float32 buffers, twice as long).
+template <typename T> struct Src;
+template <> struct Src<float> {
+    __device__ static const float *s(const UProb &P) { return P.s32; }
+    __device__ static float *u(const UProb &P) { return P.u32; }
+    __device__ static const float *om(const UProb &P) { return P.om32; }
+};
+template <> struct Src<double> {
+    __device__ static const double *s(const UProb &P) { return P.s64; }
+    __device__ static double *u(const UProb &P) { return P.u64; }
+    __device__ static const double *om(const UProb &P) { return P.omega; }
+};
+template <> struct Src<DFv> {
+    __device__ static const DFv *s(const UProb &P) { return reinterpret_cast<const DFv *>(P.s32); }
+    __device__ static DFv *u(const UProb &P) { return reinterpret_cast<DFv *>(P.u32); }
+    __device__ static const DFv *om(const UProb &P) { return reinterpret_cast<const DFv *>(P.om32); }
+};
+
+// the float copy of a float64 value in the problem's gather format
+__device__ __forceinline__ void store_copy(float *buf, int64_t i, double x, int df) {
+    if (df) reinterpret_cast<float2 *>(buf)[i] = df_from_double(x);
+    else buf[i] = (float)x;
+}
+
 // Tile loop helper: segments [s0, s1) handled by groups of g lanes over the CTA.
 // For each segment calls body(seg, lane, active) uniformly across the warp.
 template <typename F>
@@ -134,19 +192,19 @@ __device__ void tile_rows(const UProb &P, int ph, int t, const UState &S) {
     const int64_t r0 = (int64_t)t * P.rows_per_tile;
     const int64_t r1 = imin64(P.n, r0 + P.rows_per_tile);
     if (ph == PH_W) {
-        const bool f32 = sizeof(T) == 4;
+        const bool copy = !std::is_same<T, double>::value;
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             const double o = P.omega[i];
             P.u64[i] = o * P.z[i] + sqrt(o) * P.eta[i];
-            if (f32) P.om32[i] = (float)o;
+            if (copy) store_copy(P.om32, i, o, P.df);
         }
         return;
     }
     const int g = P.g_row;
     if (ph == PH_A) {
-        const T *s = sizeof(T) == 4 ? (const T *)P.s32 : (const T *)P.s64;
-        T *u = sizeof(T) == 4 ? (T *)P.u32 : (T *)P.u64;
-        const T *om = sizeof(T) == 4 ? (const T *)P.om32 : (const T *)P.omega;
+        const T *s = Src<T>::s(P);
+        T *u = Src<T>::u(P);
+        const T *om = Src<T>::om(P);
         for_segments(r0, r1, g, [&](int64_t i, int lane, bool act) {
             T acc = act ? seg_sum_coherent<T>(P.col_idx, P.row_ptr[i], P.row_ptr[i + 1], s, lane, g) : T(0);
             acc = gsum(acc, g);
@@ -179,13 +237,13 @@ __device__ void tile_cols(const UProb &P, int ph, int t, const UState &S, double
                 P.b[j] = b;
                 P.r[j] = b;
                 P.s64[j] = z;
-                P.s32[j] = (float)z;
+                store_copy(P.s32, j, z, P.df);
                 P.beta[j] = 0.0;
                 part += b * z;
             }
         });
     } else if (ph == PH_B) {
-        const T *u = sizeof(T) == 4 ? (const T *)P.u32 : (const T *)P.u64;
+        const T *u = Src<T>::u(P);
         for_segments(c0, c1, g, [&](int64_t j, int lane, bool act) {
             T acc = act ? seg_sum_coherent<T>(P.row_idx, P.col_ptr[j], P.col_ptr[j + 1], u, lane, g) : T(0);
             acc = gsum(acc, g);
@@ -233,7 +291,7 @@ __device__ void tile_vec(const UProb &P, int ph, int t, const UState &S, double 
         for (int64_t j = a + threadIdx.x; j < e; j += blockDim.x) {
             const double s = prior_var(tau, P.lambda[j]) * ldc(P.r + j) + gamma * ldc(P.s64 + j);
             P.s64[j] = s;
-            P.s32[j] = (float)s;
+            store_copy(P.s32, j, s, P.df);
         }
     }
 }
@@ -472,8 +530,22 @@ struct UnevenPlan {
     int grid = 0;
 };
 
+// Product arithmetic of the persistent kernel: float64, float32, or double-float
+// (float pairs summed with TwoSum; also serves PCG_PREC_FX64).
+enum UKind { kU64 = 0, kU32 = 1, kUDF = 2 };
+
+static UKind uneven_kind(int precision) {
+    return precision == PCG_PREC_FP64 ? kU64 : prec_pairs(precision) ? kUDF : kU32;
+}
+
+static const void *uneven_kernel(UKind k) {
+    return k == kU64 ? (const void *)k_uneven<double> : k == kUDF ? (const void *)k_uneven<DFv>
+                                                                   : (const void *)k_uneven<float>;
+}
+
 static pcg_status plan_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, const UTile &tile,
-                              bool f32, UnevenPlan *pl) {
+                              UKind kind, UnevenPlan *pl) {
+    const int fw = kind == kUDF ? 2 : 1;   // floats per copied value
     // workspace sizes
     size_t dbl = 0, flt = 0;
     std::vector<UProb> hp(nprob);
@@ -509,7 +581,8 @@ static pcg_status plan_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs,
         P.g_col = pick_g(p > 0 ? (double)pr.X_csr.nnz / p : 1.0);
         max_nt = std::max({max_nt, P.nt_col, P.nt_vec});
         dbl += 4 * (size_t)p + (size_t)n + (size_t)std::max(P.nt_col, P.nt_vec) + 8;   // b r s64 v64, u64, part
-        flt += (size_t)p + 2 * (size_t)n + 16;                                             // s32, u32, om32
+        flt += fw * ((size_t)p + 2 * (size_t)n + 16);                                      // s32, u32, om32
+        P.df = kind == kUDF ? 1 : 0;
     }
     cudaError_t e;
     char *wd = (char *)grow(ctx, "uneven_d", sizeof(double) * dbl + 256, &e);
@@ -528,10 +601,9 @@ static pcg_status plan_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs,
         P.v64 = pd; pd += a4(p);
         P.u64 = pd; pd += a4(n);
         P.part = pd; pd += a4(std::max(P.nt_col, P.nt_vec));
-        P.s32 = pf; pf += a4(p);
-        P.u32 = pf; pf += a4(n);
-        P.om32 = pf; pf += a4(n);
-        (void)f32;
+        P.s32 = pf; pf += fw * a4(p);
+        P.u32 = pf; pf += fw * a4(n);
+        P.om32 = pf; pf += fw * a4(n);
     }
     pl->d_probs = (UProb *)grow(ctx, "uneven_probs", sizeof(UProb) * nprob, &e);
     if (!pl->d_probs) return cuda_error(ctx, e, "allocating the uneven descriptors");
@@ -541,14 +613,13 @@ static pcg_status plan_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs,
     if (!pl->d_glob) return cuda_error(ctx, e, "allocating the uneven state");
     pl->h_probs = hp;
     int occ = 0;
-    PCG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          &occ, f32 ? (const void *)k_uneven<float> : (const void *)k_uneven<double>, 256, 0));
+    PCG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, uneven_kernel(kind), 256, 0));
     pl->grid = ctx->num_sms * std::max(1, std::min(occ, tile.per_sm));
     return PCG_OK;
 }
 
 // One timed or real run of the persistent kernel through a one-node graph.
-static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f32, double tol,
+static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, UKind kind, double tol,
                                 int max_iter, float *ms_out) {
     cudaError_t e;
     UProb *hp = (UProb *)grow_host(ctx, "uneven_hprobs", sizeof(UProb) * nprob, &e);
@@ -559,9 +630,8 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
     G.tol = tol;
     G.max_iter = max_iter;
     G.stop_rule = ctx->opt.stop_rule;
-    // the persistent kernel has float32 and float64 products: the double-float
-    // mode runs as float32 with float64 recomputation of r
-    G.refined = (ctx->opt.precision == PCG_PREC_FP32_REFINED || prec_pairs(ctx->opt.precision)) ? 1 : 0;
+    // float64 recomputation of r: the float32-refined mode only
+    G.refined = ctx->opt.precision == PCG_PREC_FP32_REFINED ? 1 : 0;
     G.reliable_k = ctx->opt.reliable_k;
     // give up after this long without any completed tile anywhere
     G.idle_limit_ns = (long long)llround(ctx->opt.idle_limit_s * 1e9);
@@ -581,7 +651,7 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
             return cuda_error(ctx, ce, "timing an autotune candidate");
         }
     }
-    std::string key = std::string("uneven_graph:") + (f32 ? "f" : "d") + ":" + std::to_string(pl.grid) +
+    std::string key = std::string("uneven_graph:") + std::to_string((int)kind) + ":" + std::to_string(pl.grid) +
                       ":" + std::to_string(nprob) + ":" + std::to_string((uintptr_t)pl.d_probs) + ":" +
                       std::to_string((uintptr_t)pl.d_state) + ":" + std::to_string((uintptr_t)pl.d_glob);
     if (ctx->opt.use_graph && !ctx->opt.profile) {
@@ -596,7 +666,7 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
             UGlobal *a2 = pl.d_glob;
             int a3 = nprob;
             void *args[] = {&a0, &a1, &a2, &a3};
-            kp.func = f32 ? (void *)k_uneven<float> : (void *)k_uneven<double>;
+            kp.func = (void *)uneven_kernel(kind);
             kp.gridDim = dim3(pl.grid);
             kp.blockDim = dim3(256);
             kp.kernelParams = args;
@@ -612,9 +682,13 @@ static pcg_status launch_uneven(pcg_ctx *ctx, int nprob, UnevenPlan &pl, bool f3
         PCG_CUDA_TRY(ctx, cudaGraphLaunch(exec, s));
         ctx->last_launches += 1;
     } else {
+        const UProb *a0 = pl.d_probs;
+        UState *a1 = pl.d_state;
+        UGlobal *a2 = pl.d_glob;
+        int a3 = nprob;
+        void *args[] = {&a0, &a1, &a2, &a3};
         PCG_PROF(ctx, "uneven_persistent",
-                 (f32 ? k_uneven<float><<<pl.grid, 256, 0, s>>>(pl.d_probs, pl.d_state, pl.d_glob, nprob)
-                      : k_uneven<double><<<pl.grid, 256, 0, s>>>(pl.d_probs, pl.d_state, pl.d_glob, nprob)));
+                 cudaLaunchKernel(uneven_kernel(kind), dim3(pl.grid), dim3(256), args, 0, s));
     }
     cudaError_t le = cudaGetLastError();
     if (ms_out) {
@@ -663,7 +737,7 @@ pcg_status run_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double 
 
 static pcg_status run_uneven_active(pcg_ctx *ctx, int nprob, const pcg_problem *probs, double tol,
                                     int max_iter, int *iters, double *resid, int *status) {
-    const bool f32 = ctx->opt.precision != PCG_PREC_FP64;
+    const UKind kind = uneven_kind(ctx->opt.precision);
     const std::string sig = signature(nprob, probs, ctx->opt.precision);
     UTile tile{};
     if (!load_cache(ctx, sig, &tile)) {
@@ -675,10 +749,10 @@ static pcg_status run_uneven_active(pcg_ctx *ctx, int nprob, const pcg_problem *
         UTile bt = cands[1];
         for (const UTile &c : cands) {
             UnevenPlan pl;
-            pcg_status st = plan_uneven(ctx, nprob, probs, c, f32, &pl);
+            pcg_status st = plan_uneven(ctx, nprob, probs, c, kind, &pl);
             if (st != PCG_OK) return st;
             float ms = 0.f;
-            st = launch_uneven(ctx, nprob, pl, f32, tol, max_iter, &ms);
+            st = launch_uneven(ctx, nprob, pl, kind, tol, max_iter, &ms);
             if (st != PCG_OK) return st;
             if (ms < best) {
                 best = ms;
@@ -690,9 +764,9 @@ static pcg_status run_uneven_active(pcg_ctx *ctx, int nprob, const pcg_problem *
         ctx->last_launches = 0;
     }
     UnevenPlan pl;
-    pcg_status st = plan_uneven(ctx, nprob, probs, tile, f32, &pl);
+    pcg_status st = plan_uneven(ctx, nprob, probs, tile, kind, &pl);
     if (st != PCG_OK) return st;
-    st = launch_uneven(ctx, nprob, pl, f32, tol, max_iter, nullptr);
+    st = launch_uneven(ctx, nprob, pl, kind, tol, max_iter, nullptr);
     if (st != PCG_OK) return st;
     cudaError_t e;
     UState *hs = (UState *)grow_host(ctx, "uneven_hstate", sizeof(UState) * nprob, &e);

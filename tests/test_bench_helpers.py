@@ -121,3 +121,15 @@ def test_projected_rate_arithmetic(monkeypatch):
     assert rate == pytest.approx(2 / 73.0)
     rate2, _ = bench.projected_rate([(0, 1.0, 1.0), (1, 2.0, 2.0)], 2, None)
     assert rate2 == pytest.approx(2 / 36.5)
+
+
+def test_shared_wavefronts_follow_the_same_source_guard(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({"bt_csc_df32": {
+        "source_sha": "abc", "dram_bytes_per_group": 1000, "smem_wavefronts_per_group": 40}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    assert bench.smem_wavefronts_for("bt_csc_df32", 2.0) == 80
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "changed")
+    assert bench.smem_wavefronts_for("bt_csc_df32", 2.0) is None

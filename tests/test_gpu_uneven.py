@@ -37,17 +37,14 @@ def small_batch(seed=0):
     return probs + [e, one]
 
 
-# df32 and fx64 run as fp32_refined in the persistent kernel (float32 products,
-# float64 recomputation of r)
-@pytest.mark.parametrize("prec,bound", [("fp64", 1e-6), ("fp32_refined", 1e-5), ("df32", 1e-5), ("fx64", 1e-5),
+# fx64 runs as double-float in the persistent kernel (float pairs, TwoSum)
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-6), ("fp32_refined", 1e-5), ("df32", 1e-6), ("fx64", 1e-6),
                                         ("fp32", 1e-3)])
 def test_uneven_matches_oracle(pb, prec, bound):
     probs = small_batch()
     ctx = pb.Context(precision=prec)
     res = pb.pcg_draw_beta_uneven(ctx, [as_device(pb, P) for P in probs], tol=1e-6, max_iter=20_000)
-    # the persistent kernel's products are float64 or float32: the double-float
-    # and fixed-point modes run as float32 refined
-    mode = prec if prec in ("fp64", "fp32") else "fp32_refined"
+    mode = "df32" if prec == "fx64" else prec
     for q, (P, r) in enumerate(zip(probs, res)):
         ref, k, _, st = O.draw_beta_cg(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta, tol=1e-6)
         assert r.status == pb.PCG_OK and st == O.OK, q
