@@ -148,3 +148,21 @@ def test_warm_start_solve_and_argument_checks(pb):
     assert ei.value.status == pb.PCG_BADARG
     with pytest.raises(pb.PcgError):
         pb.Context(precision="fp64", preconditioner=7)
+
+
+def test_adaptive_choice_picks_the_faster_preconditioner(pb):
+    """Sec. 3's adaptive choice with library contexts: on config 2, whose Phi
+    is strongly diagonally dominant, the Jacobi draw (6 iterations) beats the
+    prior one (about 130); every returned draw meets the stop rule for its
+    true residual."""
+    from paper_1810_12437_gb300.adaptive import AdaptivePreconditioner
+    P = inputs.config2()
+    X, a = device_problem(P)
+    ad = AdaptivePreconditioner(lambda name: pb.Context(precision="df32", preconditioner=name), period=2)
+    b = O.build_b(P.X, P.omega, P.z, P.lam, P.tau, P.eta, P.delta)
+    for step in range(3):
+        res = ad.run(step, lambda ctx: draw(pb, ctx, P, X, a, tol=1e-6, max_iter=5000))
+        assert res.status == pb.PCG_OK
+        rt = P.tau * P.lam * (b - O.phi_mul(P.X, P.omega, P.lam, P.tau, res.beta.cpu().numpy()))
+        assert np.sqrt(np.mean(rt ** 2)) <= 1.5e-6
+    assert ad.current == "jacobi" and len(ad.history) == 2
