@@ -234,38 +234,45 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def smem_wavefronts_for(kernel, groups_per_launch):
+def captured_entry(kernel, rg=None):
+    """The profiles/traffic.json entry of `kernel` if it was taken on the
+    current kernel source and, when the entry names its RHS group width, at
+    group width `rg`; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            e = json.load(f).get(kernel)
+    except Exception:
+        return None
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    if rg is not None and "rhs_group" in e and e["rhs_group"] != rg:
+        return None
+    return e
+
+
+def smem_wavefronts_for(kernel, chains_per_launch, rg=None):
     """ncu shared-memory wavefronts (l1tex__data_pipe_lsu_wavefronts_mem_shared.sum)
-    per launch, from profiles/traffic.json under the same source guard as the
-    traffic; None when absent or stale."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        e = d.get(kernel)
-        if e and e.get("source_sha") == kernel_source_sha() and "smem_wavefronts_per_group" in e:
-            return e["smem_wavefronts_per_group"] * groups_per_launch
-    except Exception:
-        pass
+    per launch: the captured launch's count, which covered `live_chains`
+    chains, scaled to `chains_per_launch` (every live chain gathers every
+    entry once); None when absent or stale."""
+    e = captured_entry(kernel, rg)
+    if e and "smem_wavefronts_per_launch" in e:
+        return e["smem_wavefronts_per_launch"] * chains_per_launch / e["live_chains"]
     return None
 
 
-def traffic_for(kernel, groups_per_launch):
+def traffic_for(kernel, alg_bytes_per_launch, n, p, nnz, rg=None):
     """ncu DRAM bytes (read + write) per launch, from profiles/traffic.json,
-    if they were taken on the current kernel source: the file holds the bytes
-    one RHS group's product moved (an all-groups-active capture divided by its
-    group count); a launch of the timed run covers `groups_per_launch` groups
-    on average."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        e = d.get(kernel)
-        if e and e.get("source_sha") == kernel_source_sha():
-            return e["dram_bytes_per_group"] * groups_per_launch
-    except Exception:
-        pass
-    return None
+    if they were taken on the current kernel source and group width.  The
+    capture is one launch with `live_chains` chains live; a timed launch with
+    fewer moves less (the index stream is read once per launch for all
+    groups, the vectors once per chain), so the captured bytes are scaled by
+    the ratio of the two launches' algorithmic bytes (survey_bytes)."""
+    e = captured_entry(kernel, rg)
+    if not e:
+        return None
+    return e["dram_bytes_per_launch"] * alg_bytes_per_launch / survey_bytes(kernel, n, p, nnz, e["live_chains"])
 
 
 def product_accounting(chain_iters, RG, tail):
@@ -346,19 +353,23 @@ def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
     ab, ib = alg_bytes(kname), impl_bytes(kname, kn)
     achieved = ab / work_launches / avg_s / 1e9 if ab else None
     impl_achieved = ib / work_launches / avg_s / 1e9 if ib else None
-    groups_per_launch = (gu / work_launches) if (gu and kname.startswith(("bt_cs", "bt_u"))) else 1.0
-    wf = smem_wavefronts_for(kname, groups_per_launch)
+    chains_per_launch = (cu / work_launches) if cu else 1.0
+    rg_k = 1 if kname.startswith("bt1_") else RG
+    wf = smem_wavefronts_for(kname, chains_per_launch, rg_k)
     smem = None
     if wf:
         # one shared-memory wavefront per clock per SM (152 SMs) at the sampled SM clock
         peak_wf = 152 * (sm_mhz or 2070.0) * 1e6
         smem = {"wavefronts_per_launch": wf, "achieved_per_s": wf / avg_s, "peak_per_s": peak_wf,
                 "frac": wf / avg_s / peak_wf,
-                "note": "ncu shared-memory wavefronts per group (profiles/traffic.json) x groups per launch, "
-                        "over the launch time; peak 1 wavefront/clock/SM"}
+                "note": "ncu shared-memory wavefronts of an all-chains-live launch (profiles/traffic.json) "
+                        "scaled by live chains per launch, over the launch time; peak 1 wavefront/clock/SM"}
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_for(kname, groups_per_launch), "shared_memory": smem,
+            "traffic": traffic_for(kname, ab / work_launches, n, p, nnz, rg_k) if ab else None,
+            "traffic_note": "ncu DRAM bytes of an all-chains-live launch (profiles/traffic.json) scaled by "
+                            "algorithmic bytes to the average working launch",
+            "shared_memory": smem,
             "peak_source": f"hbm_gbs of {peak_kind}",
             "bytes": "scope-table algorithmic bytes: int32 indices once per launch for all live "
                      "chains, vectors once per chain (survey_bytes)",
@@ -522,7 +533,7 @@ def run_ours(args):
 
 def other_forms(pb, dev, stream):
     """The uneven batch (float32 refined, float64 and double-float products)
-    and the adjoint (float32 refined), each against plain single-RHS PCG on the
+    and the adjoint (float32 refined and double-float), each against plain single-RHS PCG on the
     same GPU, precision and stop rule (RMS 1e-6)."""
     import torch
     from paper_1810_12437_gb300 import inputs
@@ -566,23 +577,26 @@ def other_forms(pb, dev, stream):
     P = inputs.config5()
     X = pb.DeviceDesign.from_host(P.X, dev)
     a = dict(omega=T(P.omega), z=T(P.z), lam=T(P.lam), eta=T(P.eta), delta=T(P.delta))
-    actx = pb.Context(precision="fp32_refined", stream=stream)
-    dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
-    pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta, T(P.c), tol=TOL)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
-    torch.cuda.synchronize(dev)
-    t_fwd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    g = pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta, T(P.c),
+    def adjoint_vs_forward(prec):
+        actx = pb.Context(precision=prec, stream=stream)
+        dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
+        pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta, T(P.c),
                        tol=TOL)
-    torch.cuda.synchronize(dev)
-    t_adj = time.perf_counter() - t0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        dr = pb.pcg_draw_beta(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], tol=TOL)
+        torch.cuda.synchronize(dev)
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        g = pb.pcg_adjoint(actx, X, a["omega"], a["z"], a["lam"], P.tau, a["eta"], a["delta"], dr.beta,
+                           T(P.c), tol=TOL)
+        torch.cuda.synchronize(dev)
+        t_adj = time.perf_counter() - t0
+        return {"forward_draws_per_s": 1.0 / t_fwd, "adjoint_gradients_per_s": 1.0 / t_adj,
+                "forward_iters": dr.iters, "adjoint_iters": g["iters"], "adjoint_over_forward_time": t_adj / t_fwd}
+
     out["adjoint"] = {"workload": "n=200000, p=20000, log10 r~U(-4,-1.8), tau=1e-3, L = c^T beta",
-                      "forward_draws_per_s": 1.0 / t_fwd, "adjoint_gradients_per_s": 1.0 / t_adj,
-                      "forward_iters": dr.iters, "adjoint_iters": g["iters"],
-                      "adjoint_over_forward_time": t_adj / t_fwd}
+                      "fp32_refined": adjoint_vs_forward("fp32_refined"), "df32": adjoint_vs_forward("df32")}
     return out
 
 

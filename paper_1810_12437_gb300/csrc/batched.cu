@@ -1381,7 +1381,7 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
     if (force && force[0]) {
         const int v = atoi(force);
         *rg_out = (v == 1 || v == 2 || v == 4 || v == 8) && v <= RP ? v : 0;
-        if (prec_pairs(ctx->opt.precision) && (*rg_out == 0 || *rg_out > 4)) *rg_out = 4 <= RP ? 4 : RP;
+        if (prec_pairs(ctx->opt.precision) && *rg_out == 0) *rg_out = 4 <= RP ? 4 : RP;   // float pairs: tiled only
         return PCG_OK;
     }
     char key[128];
@@ -1420,7 +1420,7 @@ static pcg_status choose_rg(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, 
         const int cands[] = {0, 1, 2, 4, 8};
         const bool df = prec_pairs(ctx->opt.precision);
         for (int rg : cands) {
-            if (rg > RP || (df && (rg == 0 || rg > 4))) continue;
+            if (rg > RP || (df && rg == 0)) continue;   // float-pair products exist tiled only
             BatchProducts bp;
             pcg_status st = make_products(ctx, Xr, Xc, RP, rg, &bp, false);
             if (st != PCG_OK) return st;

@@ -1138,12 +1138,26 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
 }
 
 // ---------------------------------------------------------------------------
-// CSR pass: blockIdx.x = c * csr_blocks + b, blockIdx.y = RHS group g.
+// CSR pass: block (x, g) of group_block(), x = c * csr_blocks + b, g the RHS group.
 // S: global gather source, element (j, r) of group g at
 // S[j * s_stride + s_off + g * RG + r].  Skipped when gate[g] != gate_need.
 // Writes the row partials of tile c: Pr[g][c][i][r].
 // ---------------------------------------------------------------------------
 constexpr int kStageUnroll = 16;   // staging: loads in flight per thread (8: 0.4 % slower per draw)
+
+// (slice x, RHS group g) of a product block, for launches whose gridDim.y is
+// the group count.  The blocks are numbered with the group varying fastest
+// (linear id = x * groups + g), so the blocks of every group over one slice of
+// X are dispatched together and the slice's index stream, read by each of
+// them, comes from DRAM once and from L2 for the other groups (numbered group
+// by group, each group would stream all of X's indices from DRAM again).
+struct GroupBlock {
+    int x, g;
+};
+__device__ __forceinline__ GroupBlock group_block() {
+    const unsigned lin = blockIdx.x + blockIdx.y * gridDim.x;
+    return {(int)(lin / gridDim.y), (int)(lin % gridDim.y)};
+}
 
 template <typename T, int RG>
 __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * RG), 1)
@@ -1153,11 +1167,12 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     using PT = typename Tr<T>::part;
     using SRC = typename Tr<T>::src;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = blockIdx.y;
+    const GroupBlock gb = group_block();
+    const int g = gb.g;
     if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
     SM *sS = reinterpret_cast<SM *>(smem_raw);
     const TiledPlan &P = A.plan;
-    const int c = blockIdx.x / P.csr_blocks, b = blockIdx.x % P.csr_blocks;
+    const int c = gb.x / P.csr_blocks, b = gb.x % P.csr_blocks;
     const int64_t j0 = (int64_t)c * P.W_c;
     const int64_t total = min((int64_t)P.W_c, P.p - j0) * RG;
     const int off = s_off + g * RG;
@@ -1221,7 +1236,7 @@ __global__ void __launch_bounds__(256) k_t_u(TiledArgs A, const typename Tr<T>::
 }
 
 // ---------------------------------------------------------------------------
-// CSC pass: blockIdx.x = t * csc_chunks + h, blockIdx.y = RHS group g.
+// CSC pass: block (x, g) of group_block(), x = t * csc_chunks + h, g the RHS group.
 // Stages the strip's rows of U[g] (a contiguous copy, 16 bytes per load) and
 // sums its columns' entries.  Column partial (t, j, r) goes to
 // pc_out[(t * p + j) * pc_stride + pc_off + g * RG + r].
@@ -1233,11 +1248,12 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     using SM = typename Tr<T>::smem;
     using PT = typename Tr<T>::part;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = blockIdx.y;
+    const GroupBlock gb = group_block();
+    const int g = gb.g;
     if (gate && (*(volatile const int *)(gate + g)) != gate_need) return;
     SM *sU = reinterpret_cast<SM *>(smem_raw);
     const TiledPlan &P = A.plan;
-    const int t = blockIdx.x / P.csc_chunks, h = blockIdx.x % P.csc_chunks;
+    const int t = gb.x / P.csc_chunks, h = gb.x % P.csc_chunks;
     const int64_t n = P.n, p = P.p;
     const int64_t r0 = (int64_t)t * P.W_r;
     // bytes of the strip's slice, rounded up to whole 16-byte words (the

@@ -34,17 +34,38 @@ def test_bytes_per_launch_of_the_bench_products(monkeypatch):
     assert bench.bytes_per_launch("bt_fin", N, P, NNZ, 16, 2) is None
 
 
-def test_traffic_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
+N5, P5, NNZ5 = 500_000, 50_000, 114_693_671
+
+
+def write_traffic(tmp_path, monkeypatch, entry):
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "traffic.json").write_text(json.dumps({"bt_csc_df32": {"source_sha": "abc",
-                                                                   "dram_bytes_per_group": 1000}}))
+    (prof / "traffic.json").write_text(json.dumps({"bt_csc_df32": entry}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
-    assert bench.traffic_for("bt_csc_df32", 2.5) == 2500
-    assert bench.traffic_for("bt_csr_df32", 2.5) is None        # not captured
+
+
+def test_traffic_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
+    write_traffic(tmp_path, monkeypatch, {"source_sha": "abc", "rhs_group": 2, "live_chains": 16,
+                                          "dram_bytes_per_launch": 1000, "smem_wavefronts_per_launch": 160})
+    full = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
+    assert bench.traffic_for("bt_csc_df32", full, N5, P5, NNZ5, 2) == pytest.approx(1000)
+    assert bench.traffic_for("bt_csr_df32", full, N5, P5, NNZ5, 2) is None       # not captured
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "changed")
-    assert bench.traffic_for("bt_csc_df32", 2.5) is None        # kernels changed since the capture
+    assert bench.traffic_for("bt_csc_df32", full, N5, P5, NNZ5, 2) is None       # kernels changed
+
+
+def test_traffic_scales_with_the_launch_and_group_width(tmp_path, monkeypatch):
+    """A launch with fewer live chains moves fewer algorithmic bytes and
+    gathers fewer entries; a capture at another group width is not used."""
+    write_traffic(tmp_path, monkeypatch, {"source_sha": "abc", "rhs_group": 2, "live_chains": 16,
+                                          "dram_bytes_per_launch": 1000, "smem_wavefronts_per_launch": 160})
+    half = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 8)
+    full = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
+    assert bench.traffic_for("bt_csc_df32", half, N5, P5, NNZ5, 2) == pytest.approx(1000 * half / full)
+    assert bench.smem_wavefronts_for("bt_csc_df32", 8, 2) == pytest.approx(80)
+    assert bench.traffic_for("bt_csc_df32", full, N5, P5, NNZ5, 8) is None       # captured at RG = 2
+    assert bench.smem_wavefronts_for("bt_csc_df32", 8, 8) is None
 
 
 def test_committed_traffic_matches_the_committed_kernels():
@@ -124,12 +145,8 @@ def test_projected_rate_arithmetic(monkeypatch):
 
 
 def test_shared_wavefronts_follow_the_same_source_guard(tmp_path, monkeypatch):
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    (prof / "traffic.json").write_text(json.dumps({"bt_csc_df32": {
-        "source_sha": "abc", "dram_bytes_per_group": 1000, "smem_wavefronts_per_group": 40}}))
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
-    assert bench.smem_wavefronts_for("bt_csc_df32", 2.0) == 80
+    write_traffic(tmp_path, monkeypatch, {"source_sha": "abc", "live_chains": 16,
+                                          "dram_bytes_per_launch": 1000, "smem_wavefronts_per_launch": 320})
+    assert bench.smem_wavefronts_for("bt_csc_df32", 4.0) == pytest.approx(80)
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "changed")
-    assert bench.smem_wavefronts_for("bt_csc_df32", 2.0) is None
+    assert bench.smem_wavefronts_for("bt_csc_df32", 4.0) is None

@@ -127,9 +127,9 @@ def test_batched_pair_products_match_oracle(pb, small3, prec):
 
 
 @pytest.mark.parametrize("prec", ["df32", "fx64"])
-@pytest.mark.parametrize("rg", ["1", "2", "4"])
+@pytest.mark.parametrize("rg", ["1", "2", "4", "8"])
 def test_batched_pair_products_every_group_width(pb, small3, rg, prec, monkeypatch):
-    """Double-float and fixed-point products in groups of 1, 2 and 4
+    """Double-float and fixed-point products in groups of 1, 2, 4 and 8
     right-hand sides (one launch covers every group): per chain, iteration
     counts within 2 of the oracle's float-pair band and draws within 1e-5."""
     monkeypatch.setenv("PCG_BETA_BATCH_RG", rg)
