@@ -441,12 +441,85 @@ __global__ void __launch_bounds__(kPermWarps * 32)
     }
 }
 
+// Lane-major layout.  Warp w of tile t (item q = t * nwt + w) sums the
+// segments [split[t][w], split[t][w + 1]) in rounds of 32 >> lg segments, a
+// round running nch chunk rows (nch: the round's longest segment in chunks,
+// divided by the 2^lg lanes per segment and rounded up); in row j lane l reads
+// chunk ln + j 2^lg of its segment (l = sub 2^lg + ln), or the sentinel chunk
+// past the segment's end.  k_plan_lm_rows counts each item's rows (rows[q];
+// rows[T * nwt] = 0), k_plan_lm_fill copies the chunks to their rows starting
+// at row wrow[q] (the exclusive sum of rows), one warp per item, so the
+// products read in row j exactly the chunk they would have read before.
+__device__ __forceinline__ int lm_item(const uint32_t *__restrict__ cb, const int32_t *__restrict__ split,
+                                       int64_t nseg, int nwt, int64_t q, const uint32_t **cbt, int *sA, int *sB) {
+    const int64_t t = q / nwt;
+    const int w = (int)(q - t * nwt);
+    const int32_t *sp = split + t * (nwt + 1) + w;
+    *sA = sp[0];
+    *sB = sp[1];
+    *cbt = cb + t * nseg;
+    return *sA < *sB ? lanes_log2((*cbt)[*sB] - (*cbt)[*sA], (uint32_t)(*sB - *sA)) : 0;
+}
+
+__global__ void k_plan_lm_rows(const uint32_t *__restrict__ cb, const int32_t *__restrict__ split, int64_t nseg,
+                               int T, int nwt, uint32_t *__restrict__ rows) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = (int64_t)T * nwt;
+    if (warp == 0 && lane == 0) rows[items] = 0u;
+    for (int64_t q = warp; q < items; q += nwarps) {
+        const uint32_t *cbt;
+        int sA, sB;
+        const int lg = lm_item(cb, split, nseg, nwt, q, &cbt, &sA, &sB);
+        const int spr = 32 >> lg, sub = lane >> lg;
+        uint32_t r = 0;
+        for (int base = sA; base < sB; base += spr) {
+            const int seg = base + sub;
+            const uint32_t len = seg < sB ? cbt[seg + 1] - cbt[seg] : 0u;
+            r += (__reduce_max_sync(kFull, len) + (1u << lg) - 1) >> lg;
+        }
+        if (lane == 0) rows[q] = r;
+    }
+}
+
+__global__ void k_plan_lm_fill(const uint4 *__restrict__ src, const uint32_t *__restrict__ cb,
+                               const int32_t *__restrict__ split, int64_t nseg, int T, int nwt,
+                               const uint32_t *__restrict__ wrow, uint32_t sent, uint4 *__restrict__ dst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = (int64_t)T * nwt;
+    const uint4 pad = src[sent];
+    if (warp == 0) dst[((size_t)wrow[items] << 5) + lane] = pad;   // the all-sentinel row
+    for (int64_t q = warp; q < items; q += nwarps) {
+        const uint32_t *cbt;
+        int sA, sB;
+        const int lg = lm_item(cb, split, nseg, nwt, q, &cbt, &sA, &sB);
+        const int spr = 32 >> lg, sub = lane >> lg, ln = lane & ((1 << lg) - 1);
+        size_t row = wrow[q];
+        for (int base = sA; base < sB; base += spr) {
+            const int seg = base + sub;
+            const uint32_t q0 = seg < sB ? cbt[seg] : 0u, q1 = seg < sB ? cbt[seg + 1] : 0u;
+            const uint32_t nch = (__reduce_max_sync(kFull, q1 - q0) + (1u << lg) - 1) >> lg;
+            for (uint32_t j = 0; j < nch; ++j) {
+                const uint32_t c = q0 + (uint32_t)ln + (j << lg);
+                dst[((row + j) << 5) + lane] = c < q1 ? src[c] : pad;
+            }
+            row += nch;
+        }
+    }
+}
+
 // Builds one side of the plan: padded tile-major indices, chunk bounds and
 // the per-warp work split.
 static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t *ptr,
                             const int32_t *idx, int64_t nseg, int64_t nnz, int W, int T, int nwt,
                             int value_bytes, bool bank_order, uint16_t **out_idx, uint32_t **out_cb,
-                            int32_t **out_split, uint32_t *out_sent, int32_t **out_keys, int *out_maxch) {
+                            int32_t **out_split, uint32_t *out_sent, int32_t **out_keys, int *out_maxch,
+                            bool lane_major, const uint4 **out_lm, uint32_t **out_wrow, uint32_t *out_lm_sent,
+                            bool *fits) {
+    *fits = false;
     cudaError_t e;
     const int64_t nb = (int64_t)(T + 1) * nseg;
     const int64_t nts = (int64_t)T * nseg;
@@ -467,13 +540,19 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
     const int64_t cap = ((nnz + 7 * nts + 7) & ~int64_t(7)) + 8;
     uint16_t *pidx = (uint16_t *)grow(ctx, tag + ":idx", sizeof(uint16_t) * cap, &e);
     if (!pidx) return cuda_error(ctx, e, "allocating the tiled plan");
-    size_t scan_bytes = 0, sort_bytes = 0;
+    const int64_t items = (int64_t)T * nwt;   // (tile, warp) pairs of the lane-major layout
+    uint32_t *lrows = (uint32_t *)grow(ctx, tag + ":lm_rows", sizeof(uint32_t) * (items + 1), &e);
+    if (!lrows) return cuda_error(ctx, e, "allocating the tiled plan");
+    uint32_t *wrow = (uint32_t *)grow(ctx, tag + ":wrow", sizeof(uint32_t) * (items + 1), &e);
+    if (!wrow) return cuda_error(ctx, e, "allocating the tiled plan");
+    size_t scan_bytes = 0, sort_bytes = 0, lm_scan_bytes = 0;
     int tbits = 1;
     while ((1 << tbits) < T) ++tbits;
     cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, chunks, cb, (int)nc, ctx->stream);
     cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, skeys, skeys + nts, svals, svals + nts, (int)nts, 0,
                                     32 + tbits, ctx->stream);
-    void *tmp = grow(ctx, "plan:tmp", std::max(scan_bytes, sort_bytes) + 256, &e);
+    cub::DeviceScan::ExclusiveSum(nullptr, lm_scan_bytes, lrows, wrow, (int)(items + 1), ctx->stream);
+    void *tmp = grow(ctx, "plan:tmp", std::max(std::max(scan_bytes, sort_bytes), lm_scan_bytes) + 256, &e);
     if (!tmp) return cuda_error(ctx, e, "allocating the plan scratch");
     const int grid = grid_for(ctx, 256, 8);
     cudaStream_t s = ctx->stream;
@@ -500,12 +579,36 @@ static pcg_status plan_side(pcg_ctx *ctx, const std::string &tag, const int64_t 
                  k_plan_permute<<<blocks, kPermWarps * 32, 0, s>>>(pidx, cb, split, nseg, T, nwt, nb, phase,
                                                                     (uint32_t)W));
     }
-    PCG_CUDA_TRY(ctx, cudaGetLastError());
     *out_idx = pidx;
     *out_cb = cb;
     *out_split = split;
     *out_sent = sent;
     *out_keys = order;
+    if (!lane_major) {
+        PCG_CUDA_TRY(ctx, cudaGetLastError());
+        *fits = true;
+        return PCG_OK;
+    }
+    // the lane-major copy: rows per (tile, warp), their exclusive sum, then
+    // the copy into (total + 1) rows of 32 chunks
+    k_plan_lm_rows<<<grid, 256, 0, s>>>(cb, split, nseg, T, nwt, lrows);
+    PCG_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, lm_scan_bytes, lrows, wrow, (int)(items + 1), s));
+    uint32_t *htot = (uint32_t *)grow_host(ctx, tag + ":lm_total", sizeof(uint32_t), &e);
+    if (!htot) return cuda_error(ctx, e, "allocating the tiled plan");
+    PCG_CUDA_TRY(ctx, cudaMemcpyAsync(htot, wrow + items, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    PCG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const uint64_t rows = *htot;
+    if ((rows + 1) * 32u >= (uint64_t)UINT32_MAX) return PCG_OK;   // chunk positions must fit 32 bits
+    uint4 *lm = (uint4 *)grow(ctx, tag + ":lm", sizeof(uint4) * (size_t)(rows + 1) * 32u, &e);
+    if (!lm) return cuda_error(ctx, e, "allocating the lane-major index copy");
+    PCG_PROF(ctx, "plan_lane_major",
+             k_plan_lm_fill<<<grid, 256, 0, s>>>(reinterpret_cast<const uint4 *>(pidx), cb, split, nseg, T, nwt,
+                                                 wrow, sent, lm));
+    PCG_CUDA_TRY(ctx, cudaGetLastError());
+    *out_lm = lm;
+    *out_wrow = wrow;
+    *out_lm_sent = (uint32_t)rows;
+    *fits = true;
     return PCG_OK;
 }
 
@@ -657,14 +760,18 @@ pcg_status build_tiled_plan(pcg_ctx *ctx, const char *tag, const pcg_csr *Xr, co
     pl->maxch = (int *)grow(ctx, t + ":maxch", 2 * sizeof(int), &e);
     if (!pl->maxch) return cuda_error(ctx, e, "allocating the tiled plan");
     PCG_CUDA_TRY(ctx, cudaMemsetAsync(pl->maxch, 0, 2 * sizeof(int), ctx->stream));
+    bool fits_r = false, fits_c = false;
     pcg_status st = plan_side(ctx, t + ":csr", Xr->row_ptr, Xr->col_idx, n, nnz, pl->W_c, pl->T_c,
                               pl->csr_blocks * pl->nw, RG * vsize, bank_order, &pl->col16, &pl->rt,
-                              &pl->split_r, &pl->sent_r, &pl->row_keys, pl->maxch);
+                              &pl->split_r, &pl->sent_r, &pl->row_keys, pl->maxch, true, &pl->lm_r,
+                              &pl->wrow_r, &pl->lm_sent_r, &fits_r);
     if (st != PCG_OK) return st;
+    if (!fits_r) return PCG_OK;   // untiled products (pl->valid stays false)
     st = plan_side(ctx, t + ":csc", Xc->col_ptr, Xc->row_idx, p, nnz, pl->W_r, pl->T_r, pl->csc_chunks * pl->nw,
                    RG * vsize, bank_order, &pl->row16, &pl->cs, &pl->split_c, &pl->sent_c, &pl->col_keys,
-                   pl->maxch + 1);
+                   pl->maxch + 1, false, nullptr, nullptr, nullptr, &fits_c);
     if (st != PCG_OK) return st;
+    if (!fits_c) return PCG_OK;
     // partial sums: float for float values, double otherwise (DF included);
     // row partials per group, column partials of one group (callers with
     // several groups pass their own column-partial array)
@@ -1039,25 +1146,34 @@ __device__ __forceinline__ void chunk_add(const uint4 w, const typename Tr<T>::s
 
 // One warp sums the segments [sA, sB) of a tile (rows of a column tile, or
 // columns of a row strip, in their stored order), G lanes per segment: lane
-// ln of a group reads the segment's chunks q0 + ln + G j (a group reads G
-// consecutive 16-byte chunks per load) and adds the staged values their
-// entries name; the group's lanes are summed at the end.  G (2 to 32) is
-// chosen per warp so that a typical segment of its range takes kRoundBlocks
-// blocks of kBlk chunks per lane.  The warp runs in rounds of 32 / G consecutive
-// segments; in a round every group runs the same number of chunks (the
-// round's longest segment: the CSR rows have similar lengths and the CSC
-// columns are stored by decreasing length), a lane past its segment's end
-// reading the sentinel chunk (all zero values).  The next block (of this
-// round, or the first of the next round) is loaded before the current one is
-// summed, so 2 kBlk chunks per lane are in flight.  Segment s's chunks are
-// [cb[s], cb[s + 1]); its sum goes to out[(keys ? keys[s] : s) * ostride + r].
-// fxk: the tile's fixed-point scale exponent of each right-hand side (FX only).
+// ln of a group reads the segment's chunks ln + G j and adds the staged values
+// their entries name; the group's lanes are summed at the end.  G (1 to 32)
+// is chosen per warp so that a typical segment of its range takes
+// kRoundBlocks blocks of kBlk chunks per lane.  The warp runs in rounds of
+// 32 / G consecutive segments; in a round every group runs the same number of
+// chunks (the round's longest segment: the CSR rows have similar lengths and
+// the CSC columns are stored by decreasing length), a lane past its
+// segment's end reading a sentinel chunk (all zero values).  The next block
+// (of this round, or the first of the next round) is loaded before the
+// current one is summed, so 2 kBlk chunks per lane are in flight.  Segment s's
+// chunks are [cb[s], cb[s + 1]); its sum goes to out[(keys ? keys[s] : s) *
+// ostride + r].  fxk: the tile's fixed-point scale exponent of each
+// right-hand side (FX only).
+//
+// Two index layouts (LM): the stored one, where chunk c of the tile-major
+// stream w4 is w4[c] and `sent` is the sentinel chunk, or the plan's
+// lane-major copy, where the warp's rows start at row `row0`, row j of a round
+// holds chunk j of every lane (one index load of the warp is 512 contiguous
+// bytes) and row `sent` is all sentinel chunks.  Measured on GB300 at n = 5e5,
+// p = 5e4: the lane-major copy makes the CSR pass 8-12 % faster and the CSC
+// pass 3-5 % slower, so the CSR pass reads it and the CSC pass the stored one.
 struct SegRound {
-    uint32_t q0, q1;   // this lane's segment's chunks
+    uint32_t q0, q1;   // this lane's segment's chunks (lane-major: 0 and its chunk count)
     int64_t key;
     uint32_t nch;      // chunks per lane in this round (uniform over the warp)
 };
 
+template <bool LM>
 __device__ __forceinline__ SegRound load_round(const uint32_t *__restrict__ cb, const int32_t *__restrict__ keys,
                                                int base, int sB, int sub) {
     SegRound R;
@@ -1065,8 +1181,12 @@ __device__ __forceinline__ SegRound load_round(const uint32_t *__restrict__ cb, 
     R.q0 = R.q1 = 0;
     R.key = seg;
     if (seg < sB) {
-        R.q0 = __ldg(cb + seg);
-        R.q1 = __ldg(cb + seg + 1);
+        if constexpr (LM) {
+            R.q1 = __ldg(cb + seg + 1) - __ldg(cb + seg);
+        } else {
+            R.q0 = __ldg(cb + seg);
+            R.q1 = __ldg(cb + seg + 1);
+        }
         if (keys) R.key = __ldg(keys + seg);
     }
     R.nch = 0;
@@ -1078,6 +1198,7 @@ __device__ __forceinline__ uint32_t round_chunks(const SegRound &R, int lg) {
     return (m + (1u << lg) - 1) >> lg;
 }
 
+// stored layout: chunks q0 + ln + G (j + u) of this lane's segment
 __device__ __forceinline__ void load_block(uint4 (&A)[kBlk], const uint4 *__restrict__ w4, const SegRound &R,
                                            uint32_t j, int ln, int lg, uint32_t sent) {
 #pragma unroll
@@ -1087,23 +1208,36 @@ __device__ __forceinline__ void load_block(uint4 (&A)[kBlk], const uint4 *__rest
     }
 }
 
-template <typename T, int RG>
-__device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, const uint32_t *__restrict__ cb,
-                                              int sA, int sB, const typename Tr<T>::smem *__restrict__ sv,
-                                              uint32_t sent, const int32_t *__restrict__ keys,
+// lane-major layout: rows [row, row + kBlk), this lane's chunk of each; rows
+// at or past `rend` read the sentinel row
+__device__ __forceinline__ void load_rows(uint4 (&A)[kBlk], const uint4 *__restrict__ w4, uint32_t row,
+                                          uint32_t rend, uint32_t sent_row, int lane) {
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) {
+        const uint32_t r = row + (uint32_t)u;
+        A[u] = w4[((r < rend ? r : sent_row) << 5) + (uint32_t)lane];
+    }
+}
+
+template <typename T, int RG, bool LM>
+__device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, uint32_t row0, uint32_t sent,
+                                              const uint32_t *__restrict__ cb, int sA, int sB,
+                                              const typename Tr<T>::smem *__restrict__ sv,
+                                              const int32_t *__restrict__ keys,
                                               typename Tr<T>::part *__restrict__ out, int64_t ostride,
                                               const int *fxk) {
     if (sA >= sB) return;
     const int lane = threadIdx.x & 31;
     const int lg = lanes_log2(__ldg(cb + sB) - __ldg(cb + sA), (uint32_t)(sB - sA));
     const int spr = 32 >> lg, sub = lane >> lg, ln = lane & ((1 << lg) - 1);
-    SegRound cur = load_round(cb, keys, sA, sB, sub);
+    SegRound cur = load_round<LM>(cb, keys, sA, sB, sub);
     cur.nch = round_chunks(cur, lg);
-    SegRound nxt = load_round(cb, keys, sA + spr, sB, sub);
+    SegRound nxt = load_round<LM>(cb, keys, sA + spr, sB, sub);
     int base = sA;
-    uint32_t j = 0;
+    uint32_t j = 0, rb = row0;   // rb (lane-major): the current round's first row
     uint4 A[kBlk];
-    load_block(A, w4, cur, 0, ln, lg, sent);
+    if constexpr (LM) load_rows(A, w4, rb, rb + cur.nch, sent, lane);
+    else load_block(A, w4, cur, 0, ln, lg, sent);
     Vec<T, RG> acc;
     acc.bind(fxk);
     acc.zero();
@@ -1112,8 +1246,13 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
         const bool last = j + kBlk >= cur.nch;
         if (last && base + spr < sB) nxt.nch = round_chunks(nxt, lg);
         uint4 B[kBlk];
-        if (!last) load_block(B, w4, cur, j + kBlk, ln, lg, sent);
-        else load_block(B, w4, nxt, 0, ln, lg, sent);
+        if constexpr (LM) {
+            if (!last) load_rows(B, w4, rb + j + kBlk, rb + cur.nch, sent, lane);
+            else load_rows(B, w4, rb + cur.nch, rb + cur.nch + nxt.nch, sent, lane);
+        } else {
+            if (!last) load_block(B, w4, cur, j + kBlk, ln, lg, sent);
+            else load_block(B, w4, nxt, 0, ln, lg, sent);
+        }
 #pragma unroll
         for (int u = 0; u < kBlk; ++u)
             if (j + (uint32_t)u < cur.nch) chunk_add<T, RG>(A[u], sv, acc);
@@ -1126,8 +1265,9 @@ __device__ __forceinline__ void warp_segments(const uint4 *__restrict__ w4, cons
             acc.zero();
             base += spr;
             if (base >= sB) break;
+            rb += cur.nch;
             cur = nxt;
-            nxt = load_round(cb, keys, base + spr, sB, sub);
+            nxt = load_round<LM>(cb, keys, base + spr, sB, sub);
             j = 0;
         } else {
             j += kBlk;
@@ -1155,6 +1295,7 @@ struct GroupBlock {
     int x, g;
 };
 __device__ __forceinline__ GroupBlock group_block() {
+    if (gridDim.y == 1) return {(int)blockIdx.x, 0};
     const unsigned lin = blockIdx.x + blockIdx.y * gridDim.x;
     return {(int)(lin / gridDim.y), (int)(lin % gridDim.y)};
 }
@@ -1202,11 +1343,13 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    const int32_t *__restrict__ sp = P.split_r + (size_t)c * (P.csr_blocks * P.nw + 1) + b * P.nw + warp;
+    const int wt = b * P.nw + warp;   // this warp's index within the tile
+    const int32_t *__restrict__ sp = P.split_r + (size_t)c * (P.csr_blocks * P.nw + 1) + wt;
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
+    const uint32_t row0 = __ldg(P.wrow_r + (size_t)c * (P.csr_blocks * P.nw) + wt);
     PT *__restrict__ Pr = reinterpret_cast<PT *>(P.Pr) + ((size_t)g * P.T_c + c) * (size_t)P.n * RG;
-    warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.col16), P.rt + (size_t)c * P.n, sA, sB, sS,
-                         P.sent_r, P.row_keys + (size_t)c * P.n, Pr, RG, fxk);
+    warp_segments<T, RG, true>(P.lm_r, row0, P.lm_sent_r, P.rt + (size_t)c * P.n, sA, sB, sS,
+                               P.row_keys + (size_t)c * P.n, Pr, RG, fxk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1267,15 +1410,30 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     constexpr bool fx = std::is_same<T, FX>::value;
     const int64_t nvals = min((int64_t)P.W_r, n - r0) * RG;
     uint32_t mb = 0, mb1 = 0;   // fixed point: largest |hi| of the even and odd values this thread copied
-    for (int64_t w0 = threadIdx.x; w0 < words; w0 += (int64_t)kStageUnroll * blockDim.x) {
-        uint4 v[kStageUnroll];
+    if constexpr (!fx) {
+        // asynchronous 16-byte copies straight into shared memory: every word
+        // of the slice in flight at once and no registers held (one CTA per
+        // SM, so the copy's latency is not hidden by another CTA's work)
+        const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
+        for (int64_t w = threadIdx.x; w < words; w += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + (uint32_t)(w << 4)),
+                         "l"(src + w)
+                         : "memory");
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    // fixed point reads every value it copies (its tile scale): 16-byte words
+    // through registers, half the float-pair unroll
+    constexpr int kWordUnroll = kStageUnroll / 2;
+    for (int64_t w0 = threadIdx.x; fx && w0 < words; w0 += (int64_t)kWordUnroll * blockDim.x) {
+        uint4 v[kWordUnroll];
 #pragma unroll
-        for (int k = 0; k < kStageUnroll; ++k) {
+        for (int k = 0; k < kWordUnroll; ++k) {
             const int64_t w = w0 + (int64_t)k * blockDim.x;
             if (w < words) v[k] = __ldg(src + w);
         }
 #pragma unroll
-        for (int k = 0; k < kStageUnroll; ++k) {
+        for (int k = 0; k < kWordUnroll; ++k) {
             const int64_t w = w0 + (int64_t)k * blockDim.x;
             if (w < words) {
                 dst[w] = v[k];
@@ -1300,11 +1458,12 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     if (threadIdx.x < RG) sU[(size_t)P.W_r * RG + threadIdx.x] = smem_zero<T>();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    const int32_t *__restrict__ sp = P.split_c + (size_t)t * (P.csc_chunks * P.nw + 1) + h * P.nw + warp;
+    const int wt = h * P.nw + warp;   // this warp's index within the strip
+    const int32_t *__restrict__ sp = P.split_c + (size_t)t * (P.csc_chunks * P.nw + 1) + wt;
     const int sA = __ldg(sp), sB = __ldg(sp + 1);
     PT *__restrict__ Pc = pc_out + (size_t)t * p * pc_stride + pc_off + g * RG;
-    warp_segments<T, RG>(reinterpret_cast<const uint4 *>(P.row16), P.cs + (size_t)t * p, sA, sB, sU,
-                         P.sent_c, P.col_keys + (size_t)t * p, Pc, pc_stride, fxk);
+    warp_segments<T, RG, false>(reinterpret_cast<const uint4 *>(P.row16), 0u, P.sent_c, P.cs + (size_t)t * p, sA,
+                                sB, sU, P.col_keys + (size_t)t * p, Pc, pc_stride, fxk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1386,11 +1545,11 @@ uint64_t plan_fingerprint(const TiledPlan &pl) {
         }
     };
     const void *ptrs[] = {pl.col16, pl.row16, pl.rt, pl.cs, pl.row_keys, pl.col_keys, pl.split_r, pl.split_c,
-                          pl.Pr, pl.Pc, pl.U, pl.maxch};
+                          pl.Pr, pl.Pc, pl.U, pl.maxch, pl.lm_r, pl.wrow_r};
     for (const void *q : ptrs) mix((uint64_t)(uintptr_t)q);
     const int64_t vals[] = {pl.valid, pl.RG, pl.vsize, pl.vtype, pl.ngroups, pl.n, pl.p, pl.nnz, pl.W_c, pl.T_c,
                             pl.W_r, pl.T_r, pl.u_stride, pl.csr_blocks, pl.csc_chunks, pl.threads, pl.nw,
-                            pl.sent_r, pl.sent_c, (int64_t)pl.smem_c, (int64_t)pl.smem_r};
+                            pl.sent_r, pl.sent_c, (int64_t)pl.smem_c, (int64_t)pl.smem_r, pl.lm_sent_r};
     for (int64_t v : vals) mix((uint64_t)v);
     return h;
 }

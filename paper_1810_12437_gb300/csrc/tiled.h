@@ -50,6 +50,16 @@ struct TiledPlan {
     int32_t *col_keys;        // [T_r][p]: the columns of each strip in the CSC pass's segment order
     int32_t *split_r;         // [T_c][csr_blocks * nw + 1]: first row position of each warp of a column tile
     int32_t *split_c;         // [T_r][csc_chunks * nw + 1]: first column position of each warp of a strip
+    // The lane-major copy of col16 that the CSR pass reads: the chunks of warp w
+    // of tile c are rows [wrow_r[c * nwt + w], wrow_r[c * nwt + w + 1]) of 32
+    // chunks each (nwt = csr_blocks * nw warps per tile), row j of a round
+    // holding chunk j of every lane, so that one index load of the warp reads
+    // 512 contiguous bytes.  A lane whose segment has no chunk j holds a
+    // sentinel chunk there; row lm_sent_r is all sentinel chunks (read past a
+    // warp's last round).  The CSC pass reads row16 as stored.
+    const uint4 *lm_r;
+    uint32_t *wrow_r;   // [T_c * nwt + 1]
+    uint32_t lm_sent_r;
     void *Pr;                 // row partials [ngroups][T_c][n][RG]
     void *Pc;                 // column partials [T_r][p][RG] (one group)
     void *U;                  // u = omega (.) sum_c Pr in the staged type: [ngroups][u_stride]
