@@ -275,7 +275,7 @@ def traffic_for(kernel, alg_bytes_per_launch, n, p, nnz, rg=None):
     return e["dram_bytes_per_launch"] * alg_bytes_per_launch / survey_bytes(kernel, n, p, nnz, e["live_chains"])
 
 
-def product_accounting(chain_iters, RG, tail):
+def product_accounting(chain_iters, RG, tail, RP=16):
     """Work of the tiled products in one batched draw.  In iteration k the
     live chains are those with more than k iterations (live_k); finished
     chains are compacted away, so the main plan's launch covers ceil(live_k /
@@ -283,14 +283,26 @@ def product_accounting(chain_iters, RG, tail):
     chain run the group-width-1 plan instead, and the main plan's kernels of
     those iterations exit at their gate (in the profiled plain-launch mode
     they still appear as launches).  Returns per-plan iteration counts, group
-    units and chain units (the sum of live_k)."""
+    units, chain units (the sum of live_k) and the finalize kernel's slot
+    units (the slots it covers, summed over the main plan's iterations)."""
     K = max(chain_iters) if chain_iters else 0
     live = [sum(1 for c in chain_iters if c > k) for k in range(K)]
     main = [L for L in live if not (tail and L == 1)]
     tl = [L for L in live if tail and L == 1]
+
+    def slots(L):
+        # the finalize kernel's slots: the live groups' RG slots each, rounded
+        # up to a power of two (all RP slots for the untiled products)
+        act = min(RP, -(-L // RG) * RG) if RG else RP
+        a2 = 1
+        while a2 < act:
+            a2 *= 2
+        return a2
+
     return {"iterations": K, "main_iterations": len(main), "tail_iterations": len(tl),
             "main_group_units": sum(-(-L // RG) for L in main) if RG else 0,
-            "main_chain_units": sum(main), "tail_chain_units": sum(tl)}
+            "main_chain_units": sum(main), "tail_chain_units": sum(tl),
+            "main_slot_units": sum(slots(L) for L in main), "tail_slots": slots(1)}
 
 
 def survey_bytes(kernel, n, p, nnz, L):
@@ -322,7 +334,19 @@ def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
             return acct["main_iterations"], acct["main_chain_units"], acct["main_group_units"]
         return None, None, None
 
+    def fin_bytes():
+        # k_b_fin: per column, every covered slot's strip partials (float pairs
+        # or floats), s and d read and v written (float64); with the tail plan
+        # the one chain's partials over the group-width-1 plan's strips
+        pv = 8 if PRECISION in ("df32", "fx64") else 4
+        T_main = tile_geometry(n, p, RG, pv)[1] if RG else 0
+        T_tail = tile_geometry(n, p, 1, pv)[1]
+        return p * (acct["main_slot_units"] * (pv * T_main + 24)
+                    + acct["tail_iterations"] * (pv * T_tail + 24 * acct["tail_slots"]))
+
     def impl_bytes(k, launches):
+        if k == "bt_fin":
+            return fin_bytes() if "main_slot_units" in acct else None
         it, _, gu = units(k)
         kk = k.replace("bt1_", "bt_")
         bb = bytes_per_launch(kk, n, p, nnz, RP, 1 if k.startswith("bt1_") else RG)

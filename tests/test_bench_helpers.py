@@ -102,7 +102,8 @@ def test_product_accounting_splits_main_and_tail_plans():
     and the tail plan in the last two."""
     a = bench.product_accounting([3, 1, 5], 2, tail=True)
     assert a == {"iterations": 5, "main_iterations": 3, "tail_iterations": 2,
-                 "main_group_units": 4, "main_chain_units": 7, "tail_chain_units": 2}
+                 "main_group_units": 4, "main_chain_units": 7, "tail_chain_units": 2,
+                 "main_slot_units": 4 + 2 + 2, "tail_slots": 2}
     b = bench.product_accounting([3, 1, 5], 2, tail=False)
     assert b["main_iterations"] == 5 and b["main_group_units"] == 6 and b["tail_iterations"] == 0
 
@@ -150,3 +151,17 @@ def test_shared_wavefronts_follow_the_same_source_guard(tmp_path, monkeypatch):
     assert bench.smem_wavefronts_for("bt_csc_df32", 4.0) == pytest.approx(80)
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "changed")
     assert bench.smem_wavefronts_for("bt_csc_df32", 4.0) is None
+
+
+def test_finalize_bytes_follow_the_covered_slots(monkeypatch):
+    """k_b_fin reads the strip partials of the slots it covers (4, 2, 2 in
+    the three main iterations of chains 3, 1, 5 at group width 2) and, in
+    the two tail iterations, the one chain's partials over the width-1
+    strips; s, d and v are 24 bytes per covered slot and column."""
+    monkeypatch.setattr(bench, "PRECISION", "df32")
+    acct = bench.product_accounting([3, 1, 5], 2, tail=True)
+    table = {"bt_csc_df32": (6.0, 5), "bt_fin": (1.0, 5)}
+    r = bench.roofline(table, acct, N, P, NNZ, 2, 6800.0, "measured")
+    T2, T1 = bench.tile_geometry(N, P, 2, 8)[1], bench.tile_geometry(N, P, 1, 8)[1]
+    want = P * (8 * (8 * T2 + 24) + 2 * (8 * T1 + 24 * 2))
+    assert r["per_kernel"]["bt_fin"]["impl_GBps"] == pytest.approx(want / 1e-3 / 1e9, rel=1e-3)
