@@ -992,13 +992,46 @@ struct Vec {
     __device__ __forceinline__ T out(int r) const { return v[0][r]; }
 };
 
-// Double-float sums.  A staged row holds RG values as [hi_0 .. hi_{RG-1},
-// lo_0 .. lo_{RG-1}] (for RG = 1 simply (hi, lo)), so that for even RG the his
-// and los of two right-hand sides are adjacent pairs and their TwoSums run
-// packed (two_sum2).  s: running sums, c: their accumulated rounding errors.
+// One right-hand side: the two accumulator sets (entries alternate between
+// them) live in the x and y halves of one float pair, so the two entries of
+// an index word take one packed TwoSum (the same roundings as two scalar ones).
+template <>
+struct Vec<DF, 1> {
+    float2 S, C;   // S.x, C.x: set 0's sum and accumulated errors; S.y, C.y: set 1's
+    __device__ __forceinline__ void bind(const int *) {}
+    __device__ __forceinline__ void zero() { S = C = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add_word(const float2 *b0, const float2 *b1) {
+        const float2 x0 = *b0, x1 = *b1;   // (hi, lo) of the word's two entries
+        float2 t, e;
+        two_sum2(S, make_float2(x0.x, x1.x), t, e);
+        S = t;
+        C = __fadd2_rn(C, __fadd2_rn(e, make_float2(x0.y, x1.y)));
+    }
+    __device__ __forceinline__ static void merge2(float &s0, float &c0, float s1, float c1) {
+        float t, e;
+        two_sum(s0, s1, t, e);
+        s0 = t;
+        c0 += c1 + e;
+    }
+    __device__ __forceinline__ void reduce(int lg) {
+        merge2(S.x, C.x, S.y, C.y);
+        for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(kFull, S.x, o), oc = __shfl_xor_sync(kFull, C.x, o);
+            merge2(S.x, C.x, os, oc);
+        }
+    }
+    __device__ __forceinline__ float2 out(int) const { return df_norm(S.x, C.x); }
+};
+
+// Double-float sums, RG >= 2 (RG = 1: the specialization above).  A staged
+// row holds RG values as [hi_0 .. hi_{RG-1}, lo_0 .. lo_{RG-1}] (for RG = 1
+// simply (hi, lo)), so that the his and los of two right-hand sides are
+// adjacent pairs and their TwoSums run packed (two_sum2).  s: running sums,
+// c: their accumulated rounding errors.
 template <int RG>
 struct Vec<DF, RG> {
-    static constexpr int NP = RG >= 2 ? RG / 2 : 1;   // packed pairs (RG = 1: scalar)
+    static_assert(RG >= 2, "one right-hand side uses Vec<DF, 1>");
+    static constexpr int NP = RG / 2;   // packed pairs
     float2 s[2][NP], c[2][NP];
     __device__ __forceinline__ void bind(const int *) {}
     __device__ __forceinline__ void zero() {
@@ -1010,13 +1043,7 @@ struct Vec<DF, RG> {
     template <int K>
     __device__ __forceinline__ void add_smem(const float2 *base) {
         const float *f = reinterpret_cast<const float *>(base);
-        if constexpr (RG == 1) {
-            const float2 x = *reinterpret_cast<const float2 *>(f);
-            float t, e;
-            two_sum(s[K][0].x, x.x, t, e);
-            s[K][0].x = t;
-            c[K][0].x += e + x.y;
-        } else if constexpr (RG == 2) {
+        if constexpr (RG == 2) {
             const float4 x = *reinterpret_cast<const float4 *>(f);   // hi0 hi1 lo0 lo1
             add_pair<K>(0, make_float2(x.x, x.y), make_float2(x.z, x.w));
         } else {
@@ -1046,18 +1073,16 @@ struct Vec<DF, RG> {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             merge2(s[0][q].x, c[0][q].x, s[1][q].x, c[1][q].x);
-            if (RG >= 2) merge2(s[0][q].y, c[0][q].y, s[1][q].y, c[1][q].y);
+            merge2(s[0][q].y, c[0][q].y, s[1][q].y, c[1][q].y);
         }
         for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 float os = __shfl_xor_sync(kFull, s[0][q].x, o), oc = __shfl_xor_sync(kFull, c[0][q].x, o);
                 merge2(s[0][q].x, c[0][q].x, os, oc);
-                if (RG >= 2) {
-                    os = __shfl_xor_sync(kFull, s[0][q].y, o);
-                    oc = __shfl_xor_sync(kFull, c[0][q].y, o);
-                    merge2(s[0][q].y, c[0][q].y, os, oc);
-                }
+                os = __shfl_xor_sync(kFull, s[0][q].y, o);
+                oc = __shfl_xor_sync(kFull, c[0][q].y, o);
+                merge2(s[0][q].y, c[0][q].y, os, oc);
             }
         }
     }
@@ -1139,8 +1164,12 @@ __device__ __forceinline__ void chunk_add(const uint4 w, const typename Tr<T>::s
     const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-        acc.template add_smem<0>(sv + (wd[h] & 0xffffu) * RG);
-        acc.template add_smem<1>(sv + (wd[h] >> 16) * RG);
+        if constexpr (std::is_same<T, DF>::value && RG == 1) {
+            acc.add_word(sv + (wd[h] & 0xffffu), sv + (wd[h] >> 16));   // both entries in one packed TwoSum
+        } else {
+            acc.template add_smem<0>(sv + (wd[h] & 0xffffu) * RG);
+            acc.template add_smem<1>(sv + (wd[h] >> 16) * RG);
+        }
     }
 }
 
@@ -1319,8 +1348,33 @@ __global__ void __launch_bounds__(tiled_threads(sizeof(typename Tr<T>::smem) * R
     const int off = s_off + g * RG;
     constexpr bool fx = std::is_same<T, FX>::value;
     uint32_t mb = 0;   // fixed point: largest |hi| this thread staged (float bits)
-    // stage the tile's slice of s, kStageUnroll loads in flight per thread
-    for (int64_t t0 = threadIdx.x; t0 < total; t0 += (int64_t)kStageUnroll * blockDim.x) {
+    bool direct = false;
+    if constexpr (!fx && (std::is_same<T, float>::value || std::is_same<T, double>::value ||
+                          (std::is_same<T, DF>::value && RG == 1))) {
+        // The staged layout is the source's here.  When the slice is
+        // contiguous in global memory (one group: s_stride == RG) and 16-byte
+        // aligned, copy it with cp.async: the whole slice in flight and no
+        // registers held (one CTA per SM: nothing else hides the latency).
+        const SRC *src = S + j0 * RG + off;
+        direct = s_stride == RG && (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+        if (direct) {
+            const int64_t words = (total * (int64_t)sizeof(SRC)) >> 4;
+            const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(sS);
+            const uint4 *src4 = reinterpret_cast<const uint4 *>(src);
+            for (int64_t w = threadIdx.x; w < words; w += blockDim.x)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + (uint32_t)(w << 4)),
+                             "l"(src4 + w)
+                             : "memory");
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            // values past the last whole 16-byte word
+            for (int64_t t = ((words << 4) / (int64_t)sizeof(SRC)) + threadIdx.x; t < total; t += blockDim.x)
+                sS[t] = __ldg(src + t);
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        }
+    }
+    // otherwise stage the tile's slice of s through registers, kStageUnroll
+    // loads in flight per thread
+    for (int64_t t0 = threadIdx.x; !direct && t0 < total; t0 += (int64_t)kStageUnroll * blockDim.x) {
         SRC v[kStageUnroll];
 #pragma unroll
         for (int k = 0; k < kStageUnroll; ++k) {
