@@ -10,6 +10,10 @@ the per-kernel averages.  --full instead runs every chain to the stop rule
 (tol 1e-6), as a whole draw of the benchmark does.  --small uses a 20x smaller
 design (n=25,000, p=2,500) of the same recipe; --rg fixes the batched path's
 RHS group width (otherwise it is autotuned).
+
+`uneven` runs one uneven-batch draw of 16 problems of the uneven recipe
+(n ~ logU[5e3, 6e4], p ~ logU[1e3, 1e4]) to the stop rule (tol 1e-6) in the
+persistent kernel, and prints the iteration total and the statuses.
 """
 import os
 import argparse
@@ -24,7 +28,7 @@ from . import inputs
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["single", "batched"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "uneven"], default="single")
     ap.add_argument("--iters", type=int, default=6)
     ap.add_argument("--precision", default="fp32_refined")
     ap.add_argument("--small", action="store_true")
@@ -37,6 +41,16 @@ def main(argv=None):
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
     kw = dict(n=25_000, p=2_500) if args.small else {}
     tol, max_iter = (1e-6, 20_000) if args.full else (0.0, args.iters)
+    if args.workload == "uneven":
+        probs = inputs.config4(nprob=16, n_range=(5_000, 60_000), p_range=(1_000, 10_000))
+        dp = [dict(X=pb.DeviceDesign.from_host(P.X, dev), omega=T(P.omega), z=T(P.z), lam=T(P.lam),
+                   tau=float(P.tau), eta=T(P.eta), delta=T(P.delta)) for P in probs]
+        ctx = pb.Context(precision=args.precision)
+        res = pb.pcg_draw_beta_uneven(ctx, dp, tol=1e-6, max_iter=20_000)
+        torch.cuda.synchronize()
+        print(json.dumps({"problems": len(dp), "nnz": int(sum(P.X.nnz for P in probs)),
+                          "iters": int(sum(r.iters for r in res)), "status": [int(r.status) for r in res]}))
+        return
     if args.workload == "single":
         P = inputs.config3(nrhs=1, **kw)
         X = pb.DeviceDesign.from_host(P.X, dev)
