@@ -268,11 +268,11 @@ def traffic_for(kernel, alg_bytes_per_launch, n, p, nnz, rg=None):
     capture is one launch with `live_chains` chains live; a timed launch with
     fewer moves less (the index stream is read once per launch for all
     groups, the vectors once per chain), so the captured bytes are scaled by
-    the ratio of the two launches' algorithmic bytes (survey_bytes)."""
+    the ratio of the two launches' algorithmic bytes (scope_table_bytes)."""
     e = captured_entry(kernel, rg)
     if not e:
         return None
-    return e["dram_bytes_per_launch"] * alg_bytes_per_launch / survey_bytes(kernel, n, p, nnz, e["live_chains"])
+    return e["dram_bytes_per_launch"] * alg_bytes_per_launch / scope_table_bytes(kernel, n, p, nnz, e["live_chains"])
 
 
 def product_accounting(chain_iters, RG, tail, RP=16):
@@ -305,7 +305,7 @@ def product_accounting(chain_iters, RG, tail, RP=16):
             "main_slot_units": sum(slots(L) for L in main), "tail_slots": slots(1)}
 
 
-def survey_bytes(kernel, n, p, nnz, L):
+def scope_table_bytes(kernel, n, p, nnz, L):
     """Algorithmic bytes of one product pass over L live chains by the
     hot-path scope table's measure (binary X as int32 indices read once for
     the whole RHS block, int64 pointers, float32 gathered vectors read once,
@@ -321,7 +321,7 @@ def survey_bytes(kernel, n, p, nnz, L):
 
 def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
     """Roofline entry of the dominant kernel and the per-kernel table.
-    `achieved` uses the scope table's algorithmic bytes (survey_bytes) summed
+    `achieved` uses the scope table's algorithmic bytes (scope_table_bytes) summed
     over the launches that did work, divided by the kernel's total CUDA-event
     time; `impl_*` gives the same with the kernel's own per-group bytes
     (bytes_per_launch: 16-bit tile offsets, staged slices, tile partials)."""
@@ -356,10 +356,10 @@ def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
 
     def alg_bytes(k):
         it, cu, _ = units(k)
-        if it is None or survey_bytes(k, n, p, nnz, 1) is None:
+        if it is None or scope_table_bytes(k, n, p, nnz, 1) is None:
             return None
         return it * (4 * nnz + 8 * ((n if "csr" in k else p) + 1)) + (
-            survey_bytes(k, n, p, nnz, 1) - survey_bytes(k, n, p, nnz, 0)) * cu
+            scope_table_bytes(k, n, p, nnz, 1) - scope_table_bytes(k, n, p, nnz, 0)) * cu
 
     total_ms = sum(v[0] for v in table.values())
     per_k = {}
@@ -396,7 +396,7 @@ def roofline(table, acct, n, p, nnz, RG, peak, peak_kind, sm_mhz=None):
             "shared_memory": smem,
             "peak_source": f"hbm_gbs of {peak_kind}",
             "bytes": "scope-table algorithmic bytes: int32 indices once per launch for all live "
-                     "chains, vectors once per chain (survey_bytes)",
+                     "chains, vectors once per chain (scope_table_bytes)",
             "avg_launch_us": avg_s * 1e6, "working_launches": work_launches,
             "launches_profiled": kn,
             "algorithmic_bytes_per_launch": ab / work_launches if ab else None,

@@ -48,7 +48,7 @@ def write_traffic(tmp_path, monkeypatch, entry):
 def test_traffic_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
     write_traffic(tmp_path, monkeypatch, {"source_sha": "abc", "rhs_group": 2, "live_chains": 16,
                                           "dram_bytes_per_launch": 1000, "smem_wavefronts_per_launch": 160})
-    full = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
+    full = bench.scope_table_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
     assert bench.traffic_for("bt_csc_df32", full, N5, P5, NNZ5, 2) == pytest.approx(1000)
     assert bench.traffic_for("bt_csr_df32", full, N5, P5, NNZ5, 2) is None       # not captured
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "changed")
@@ -60,8 +60,8 @@ def test_traffic_scales_with_the_launch_and_group_width(tmp_path, monkeypatch):
     gathers fewer entries; a capture at another group width is not used."""
     write_traffic(tmp_path, monkeypatch, {"source_sha": "abc", "rhs_group": 2, "live_chains": 16,
                                           "dram_bytes_per_launch": 1000, "smem_wavefronts_per_launch": 160})
-    half = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 8)
-    full = bench.survey_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
+    half = bench.scope_table_bytes("bt_csc_df32", N5, P5, NNZ5, 8)
+    full = bench.scope_table_bytes("bt_csc_df32", N5, P5, NNZ5, 16)
     assert bench.traffic_for("bt_csc_df32", half, N5, P5, NNZ5, 2) == pytest.approx(1000 * half / full)
     assert bench.smem_wavefronts_for("bt_csc_df32", 8, 2) == pytest.approx(80)
     assert bench.traffic_for("bt_csc_df32", full, N5, P5, NNZ5, 8) is None       # captured at RG = 2
@@ -108,16 +108,16 @@ def test_product_accounting_splits_main_and_tail_plans():
     assert b["main_iterations"] == 5 and b["main_group_units"] == 6 and b["tail_iterations"] == 0
 
 
-def test_survey_bytes_share_the_index_streams():
+def test_scope_table_bytes_share_the_index_streams():
     """The scope table's bytes: one CSC pass over 16 chains reads the 4-byte
     row indices once, each chain's vectors once: about 1.04 GB for the two
     product passes of one 16-chain iteration (the table's 1.09 GB per
     iteration adds the CG update's vectors)."""
-    one = bench.survey_bytes("bt_csc_df32", N, P, NNZ, 1)
-    sixteen = bench.survey_bytes("bt_csc_df32", N, P, NNZ, 16)
+    one = bench.scope_table_bytes("bt_csc_df32", N, P, NNZ, 1)
+    sixteen = bench.scope_table_bytes("bt_csc_df32", N, P, NNZ, 16)
     assert one == 4 * NNZ + 8 * (P + 1) + 4 * N + 24 * P
     assert sixteen - one == 15 * (4 * N + 24 * P)
-    both = sixteen + bench.survey_bytes("bt_csr_df32", N, P, NNZ, 16)
+    both = sixteen + bench.scope_table_bytes("bt_csr_df32", N, P, NNZ, 16)
     assert 1.03e9 < both < 1.05e9
 
 
