@@ -270,7 +270,11 @@ pcg_status pcg_solve(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
  * chain-major.  iters, resid, status (host, nrhs each) receive each chain's
  * result; the return value is the worst status.  1 <= nrhs <= 32.
  * Precisions PCG_PREC_DF32, PCG_PREC_FX64, PCG_PREC_FP32_REFINED and
- * PCG_PREC_FP32 (PCG_PREC_FP64 returns PCG_BADARG).
+ * PCG_PREC_FP32 (PCG_PREC_FP64 returns PCG_BADARG).  PCG_PREC_DF32 and
+ * PCG_PREC_FX64 exist only as tiled products: for a design beyond the tiled
+ * plan's 32-bit positions (pcg_tiled_plan_applies false with nonzeros;
+ * about 4e9 of them) they return PCG_BADARG, and the float32 modes run
+ * untiled.
  */
 pcg_status pcg_draw_beta_batched(pcg_ctx *ctx, const pcg_csr *X_csr, const pcg_csc *X_csc,
                                  int nrhs, const double *omega, const double *z,

@@ -1556,6 +1556,12 @@ pcg_status run_batched(pcg_ctx *ctx, const pcg_csr *Xr, const pcg_csc *Xc, int n
     BatchProducts bp;
     st = make_products(ctx, Xr, Xc, RP, RG, &bp, true);
     if (st != PCG_OK) return st;
+    // float pairs exist only in the tiled products (the untiled kernels read
+    // float32 copies; with no nonzero they gather nothing)
+    if (prec_pairs(ctx->opt.precision) && !bp.RG && Xr->nnz > 0)
+        return set_error(ctx, PCG_BADARG, "PCG_PREC_DF32 and PCG_PREC_FX64 need the tiled products, which do not "
+                                          "apply to this design (too large for their 32-bit positions): use "
+                                          "PCG_PREC_FP32_REFINED");
     ctx->last_launches = 0;
     d.RG = bp.RG;
     d.tail = bp.tail ? 1 : 0;
