@@ -580,8 +580,10 @@ static pcg_status plan_uneven(pcg_ctx *ctx, int nprob, const pcg_problem *probs,
         P.g_row = pick_g(n > 0 ? (double)pr.X_csr.nnz / n : 1.0);
         P.g_col = pick_g(p > 0 ? (double)pr.X_csr.nnz / p : 1.0);
         max_nt = std::max({max_nt, P.nt_col, P.nt_vec});
-        dbl += 4 * (size_t)p + (size_t)n + (size_t)std::max(P.nt_col, P.nt_vec) + 8;   // b r s64 v64, u64, part
-        flt += fw * ((size_t)p + 2 * (size_t)n + 16);                                      // s32, u32, om32
+        // exactly what the carving below takes (each array rounded up to 4 elements)
+        auto r4 = [](int64_t x) { return (size_t)((x + 3) & ~int64_t(3)); };
+        dbl += 4 * r4(p) + r4(n) + r4(std::max(P.nt_col, P.nt_vec));   // b r s64 v64, u64, part
+        flt += fw * (r4(p) + 2 * r4(n));                                 // s32, u32, om32
         P.df = kind == kUDF ? 1 : 0;
     }
     cudaError_t e;
@@ -744,7 +746,8 @@ static pcg_status run_uneven_active(pcg_ctx *ctx, int nprob, const pcg_problem *
         // autotune: time the whole batch for each candidate tile shape and keep
         // the fastest (the candidates' results are recomputed below)
         const UTile cands[] = {{256, 64, 8192, 8},   {1024, 128, 8192, 8}, {4096, 512, 16384, 8},
-                               {1024, 256, 16384, 4}, {512, 64, 4096, 6},  {2048, 256, 8192, 6}};
+                               {1024, 256, 16384, 4}, {512, 64, 4096, 6},  {2048, 256, 8192, 6},
+                               {128, 32, 4096, 8},    {64, 16, 2048, 8}};
         float best = 1e30f;
         UTile bt = cands[1];
         for (const UTile &c : cands) {
